@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Throughput of the projected t-SVD hot path (*Q-SVDII, Alg. 4.2) on GB300.
+
+One step = one tsvdqII call through the C ABI on the video-shaped workload
+(A 120 x 160 x 300 FP32, Q = leading p = 50 left singular vectors of the mode-3
+unfolding, gamma = 0.99): projection, facewise Jacobi SVDs, global energy
+selection, truncated factors, low-rank rebuild, back-projection and the error
+terms.  Metric: tensor entries compressed per second (l*m*n / step time).
+
+Our arm:       python bench.py [--gpus N --steps K --warmup W]
+Reference arm: python bench.py --impl reference ...   (the FP64 CPU oracle)
+
+Timing: inputs resident in HBM; L2 flushed (256 MiB write) before every step,
+outside the per-step CUDA events; K steps bracketed by barrier + synchronize;
+max over ranks.  The same line carries the p = n (*M) run at equal
+reconstruction error, the roofline of the dominant kernel (the Jacobi SVD,
+timed live with stage events on the launching stream), the end-to-end number
+through host buffers, the oracle CPU baseline and the SM clocks sampled during
+the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L, M, N, P, GAMMA = 120, 160, 300, 50, 0.99
+WORKLOAD = "video-shaped tSVDQII 120x160x300 (l x m x frames), Q = U3 leading p=50, gamma=0.99"
+METRIC = "tensor entries compressed/sec (tSVDQ)"
+UNIT = "entries/s"
+FP32_LANES_PER_SM, SMS = 128, 152
+
+
+def nominal_svd_flops(l, m, p):
+    """Textbook Golub-Kahan-Reinsch count for sigma and V of an a x b slice
+    (a >= b): 4ab^2 + 8b^3, times p slices."""
+    a, b = max(l, m), min(l, m)
+    return p * (4.0 * a * b * b + 8.0 * b ** 3)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi SM clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs():
+    from paper_2409_19402_gb300 import inputs
+    A = inputs.video(l=L, m=M, n=N)
+    Qp = inputs.u3_q(A, P)
+    Qn = inputs.u3_q(A, N)
+    return A, Qp, Qn
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    A, Qp, _ = make_inputs()
+    for _ in range(args.warmup):
+        oracle.tsvdqII(A, Qp, GAMMA)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.tsvdqII(A, Qp, GAMMA)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = L * M * N * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l": L, "m": M, "n": N, "p": P, "gamma": GAMMA},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "each step: one full oracle tsvdqII of the workload"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+class Runner:
+    """Preallocated buffers and a direct C-ABI call for one tsvdqII configuration."""
+
+    def __init__(self, A_dev, Q_dev, gamma, torch, binding):
+        import ctypes
+        self.t, self.b, self.ct = torch, binding, ctypes
+        self.A, self.Q, self.gamma = A_dev, Q_dev, gamma
+        n, l, m = A_dev.shape
+        p = Q_dev.shape[1]
+        r = min(l, m)
+        self.dims = (l, m, n, p)
+        d = A_dev.device
+        self.rho = torch.empty(p, dtype=torch.int32, device=d)
+        self.offs = torch.empty(p + 1, dtype=torch.int64, device=d)
+        self.Uh = torch.empty(p * r * l, dtype=torch.float32, device=d)
+        self.s = torch.empty(p * r, dtype=torch.float32, device=d)
+        self.Vh = torch.empty(p * r * m, dtype=torch.float32, device=d)
+        self.Ak = torch.empty((n, l, m), dtype=torch.float32, device=d)
+        self.rep = torch.zeros(binding.REPORT_BYTES, dtype=torch.uint8, device=d)
+        nb = binding.workspace_bytes(binding.PP_OP_TSVDQII, l=l, m=m, n=n, p=p)
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=d)
+        self.opts = binding.pp_opts()
+
+    def __call__(self, stream):
+        P_ = lambda x: self.ct.c_void_p(x.data_ptr())
+        l, m, n, p = self.dims
+        st = self.b.lib().tsvdqII(P_(self.A), P_(self.Q), l, m, n, p, float(self.gamma),
+                                  P_(self.rho), P_(self.offs), P_(self.Uh), P_(self.s),
+                                  P_(self.Vh), P_(self.Ak), P_(self.rep),
+                                  self.ct.byref(self.opts), P_(self.ws), self.ws.numel(),
+                                  self.ct.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(self.b.status_str(st))
+
+    def report(self):
+        return self.b.read_report(self.rep)
+
+
+def timed_steps(run, steps, warmup, torch, flush, stream, stage_events=None):
+    """Per-step CUDA-event times (ms) with an L2 flush before every step."""
+    for _ in range(warmup):
+        flush.zero_()
+        run(stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    stage_ms = []
+    times = []
+    for i in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            evs[i][0].record(stream)
+            run(stream)
+            evs[i][1].record(stream)
+        if stage_events is not None:
+            stream.synchronize()
+            stage_ms.append([stage_events[j].elapsed_time(stage_events[j + 1])
+                             for j in range(len(stage_events) - 1)])
+    torch.cuda.synchronize()
+    times = [a.elapsed_time(b) for a, b in evs]
+    return times, stage_ms
+
+
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2409_19402_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    binding.lib()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    A, Qp, Qn = make_inputs()
+    A_d = torch.from_numpy(A).to(dev)
+    Qp_d = torch.from_numpy(Qp).to(dev)
+    Qn_d = torch.from_numpy(Qn).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    run = Runner(A_d, Qp_d, GAMMA, torch, binding)
+
+    # stage events: created by recording once, then registered with the library
+    stage_events = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in stage_events:
+        e.record(stream)
+    stream.synchronize()
+    binding.set_stage_events(stage_events)
+
+    # ---------------- timed region (p < n)
+    launches0 = binding.kernel_launches()
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times, stage_ms = timed_steps(run, args.steps, args.warmup, torch, flush, stream,
+                                  stage_events)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    launches = binding.kernel_launches() - launches0
+    per_step_launches = launches / (args.steps + args.warmup)
+    binding.set_stage_events(None)
+    rep = run.report()
+    if rep.status != 0:
+        raise RuntimeError(f"device status {binding.status_str(rep.status)}")
+
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * L * M * N * args.steps / (total_ms / 1e3)
+
+    # ---------------- dominant kernel roofline (Jacobi SVD, stage 1 -> 2)
+    peaks, peak_kind = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+    stage_mean = [statistics.mean(s[j] for s in stage_ms) for j in range(5)]
+    jac_ms = stage_mean[1]
+    flops = nominal_svd_flops(L, M, P)
+    achieved = flops / (jac_ms / 1e3) / 1e12
+    roofline = {"kernel": "jacobi_kernel (facewise one-sided Jacobi SVD)", "bound": "alu",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": None,
+                "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
+                "work": "nominal 4ab^2+8b^3 per slice (Golub-Kahan-Reinsch), p=50"}
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    proj_bytes = 4.0 * (L * M * N + N * P + P * L * M)
+    back_bytes = 4.0 * (L * M * N * 2 + P * L * M + N * P)  # read A_k-hat and A, write A_k
+    stages = {"projection_ms": stage_mean[0], "jacobi_ms": stage_mean[1],
+              "select_ms": stage_mean[2], "factors_rebuild_ms": stage_mean[3],
+              "backproj_errors_ms": stage_mean[4],
+              "projection_hbm_frac": proj_bytes / (stage_mean[0] / 1e3) / 1e9 / hbm,
+              "backproj_hbm_frac": back_bytes / (stage_mean[4] / 1e3) / 1e9 / hbm}
+
+    # ---------------- p = n (*M) at equal reconstruction error
+    pn = None
+    if not args.no_pn:
+        err_target = rep.err2
+        full = binding.tsvdq_trunc(A_d, Qn_d, min(L, M), want_ak=False)
+        torch.cuda.synchronize()
+        sig = full.s.double().cpu().numpy()
+        keys = np.sort((sig ** 2).ravel())[::-1]
+        c = np.cumsum(keys)
+        total = c[-1]
+        frep = full.report()
+        proj = max(frep.normA2 - frep.normAh2, 0.0)
+        need = total - (err_target - proj)          # kept energy needed
+        Kp = int(np.searchsorted(c, need, side="left")) + 1
+        Kp = min(max(Kp, 1), len(c))
+        gamma_pn = min(1.0, c[Kp - 1] / total)
+        run_pn = Runner(A_d, Qn_d, gamma_pn, torch, binding)
+        t_pn, _ = timed_steps(run_pn, args.steps, args.warmup, torch, flush, stream)
+        rpn = run_pn.report()
+        ms_pn = sum(t_pn) / args.steps
+        pn = {"p": N, "gamma": gamma_pn, "ms_per_step": ms_pn,
+              "value": L * M * N / (ms_pn / 1e3), "err2": rpn.err2, "err2_target": err_target,
+              "kappa": int(rpn.kappa), "speedup_p_lt_n": ms_pn / ms_per_step}
+
+    # ---------------- end to end through host buffers (pinned)
+    A_h = torch.from_numpy(A).pin_memory()
+    Q_h = torch.from_numpy(Qp).pin_memory()
+    e2e_times = []
+    d2h_bytes = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            run.A.copy_(A_h, non_blocking=True)
+            run.Q.copy_(Q_h, non_blocking=True)
+            run(stream)
+            hdr = torch.empty(binding.REPORT_BYTES, dtype=torch.uint8).pin_memory()
+            hdr.copy_(run.rep, non_blocking=True)
+            rho_h = run.rho.to("cpu", non_blocking=True)
+            offs_h = run.offs.to("cpu", non_blocking=True)
+        stream.synchronize()
+        kappa = int(offs_h[-1])
+        with torch.cuda.stream(stream):
+            U_h = run.Uh[:kappa * L].to("cpu", non_blocking=True)
+            s_h = run.s[:kappa].to("cpu", non_blocking=True)
+            V_h = run.Vh[:kappa * M].to("cpu", non_blocking=True)
+        stream.synchronize()
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            e2e_times.append(dt)
+            d2h_bytes.append(binding.REPORT_BYTES + rho_h.numel() * 4 + offs_h.numel() * 8 +
+                             4 * (U_h.numel() + s_h.numel() + V_h.numel()))
+    e2e_s = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * L * M * N * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(A.nbytes + Qp.nbytes),
+           "d2h_bytes_per_step": int(statistics.mean(d2h_bytes)),
+           "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    # ---------------- oracle CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.tsvdqII(A, Qp, GAMMA)
+        dt = time.perf_counter() - t0
+        cpu = {"value": L * M * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
+               "seconds": dt}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l": L, "m": M, "n": N, "p": P, "gamma": GAMMA,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single",
+                       "l2": "flushed before every step (256 MiB write), outside the events",
+                       "K": int(rep.K), "kappa": int(rep.kappa), "sweeps": int(rep.sweeps),
+                       "RE": math.sqrt(rep.err2 / rep.normA2)},
+            "roofline": roofline,
+            "stages": stages,
+            "pn_compare": pn,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": int(round(per_step_launches * args.steps)),
+            "clocks": clk,
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * pprod.h -- C ABI of the GB300 (sm_103a) projected tensor-tensor product
+ * library: the projected t-SVD hot path of Keegan & Newman, "Projected
+ * Tensor-Tensor Products for Efficient Computation of Optimal Multiway Data
+ * Representations" (arXiv 2409.19402).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Tensors.  An n1 x n2 x n3 tensor T is stored frontal-slice-major in FP32:
+ *   entry (i, j, t) (0-based) at T[(t*n1 + i)*n2 + j].
+ * Frontal slice t is a contiguous row-major n1 x n2 matrix and the mode-3
+ * unfolding T_(3) (Def. 2.1) is the row-major n3 x (n1*n2) matrix at the same
+ * address (pixel order (i, j) row-major instead of the paper's column-major
+ * J(i,j); the mode-3 product acts tube by tube, so this changes nothing).
+ * This is a C-contiguous PyTorch tensor of shape (n3, n1, n2).
+ *
+ * Q.  The transformation is a real n x p matrix with orthonormal columns
+ * (Q in St_{n,p}, Sec. 3), row-major FP32 (Q[s*p + t]).  With p = n and Q
+ * square orthogonal every call computes the invertible *M form (Def. 2.4,
+ * M = Q^T).  Complex Q is not supported.
+ *
+ * Pointers.  Every array argument is a DEVICE pointer, unless stated
+ * otherwise, owned by the caller: the library never allocates or frees
+ * device memory.  Inputs are read only.  Outputs must not alias inputs.
+ * Calls needing scratch take a caller-allocated device workspace of at least
+ * pp_workspace_bytes(op, shape) bytes, 256-byte aligned.
+ *
+ * Execution.  Every call is asynchronous on `stream` (a cudaStream_t passed
+ * as void*; NULL = legacy default stream) and returns after enqueueing.
+ * Results, including the device-side pp_report, are valid after the stream
+ * is synchronised.  The call makes no host<->device copies and no stream or
+ * device synchronisation.
+ *
+ * Errors.  Argument errors the host can see (bad sizes, NULL pointers, a
+ * workspace that is too small, gamma outside (0, 1]) return a nonzero
+ * pp_status before anything is enqueued.  A failed kernel launch returns
+ * PP_ECUDA.  Conditions only the device can see (Q not orthonormal, a
+ * non-finite input, Jacobi not converged within the sweep cap) are written to
+ * pp_report.status; the outputs are then unspecified.  Nothing in the library
+ * aborts, exits or traps.
+ */
+#ifndef PPROD_H
+#define PPROD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of this ABI are the only ones the shared library exports. */
+#if defined(__GNUC__)
+#define PP_API __attribute__((visibility("default")))
+#else
+#define PP_API
+#endif
+
+typedef enum pp_status {
+    PP_OK = 0,
+    PP_EINVAL = 1,      /* bad scalar argument or NULL pointer                 */
+    PP_ESHAPE = 2,      /* inconsistent or out-of-range sizes                 */
+    PP_ENOTORTHO = 3,   /* device: max |Q^T Q - I| above opts->q_tol           */
+    PP_ENONFINITE = 4,  /* device: NaN/Inf in the input tensor                 */
+    PP_ENOCONV = 5,     /* device: Jacobi did not converge within max_sweeps   */
+    PP_ETIMEOUT = 6,    /* device: a bounded wait gave up                      */
+    PP_EWORKSPACE = 7,  /* workspace NULL, misaligned or smaller than needed   */
+    PP_ECUDA = 8,       /* a CUDA launch or runtime call failed                */
+    PP_ENOSYS = 9       /* requested variant not built                         */
+} pp_status;
+
+/* Operation selector for pp_workspace_bytes. */
+typedef enum pp_op {
+    PP_OP_MODE3 = 0,
+    PP_OP_FACEWISE = 1,
+    PP_OP_PPROD = 2,
+    PP_OP_TSVDQ = 3,
+    PP_OP_TSVDQII = 4
+} pp_op;
+
+/* Problem sizes for pp_workspace_bytes.  Fields an op does not use are
+ * ignored.  l x m x n is the tensor A (n frontal slices), p the projection
+ * dimension, k the fixed truncation, n2 the second dimension of B in pprod. */
+typedef struct pp_shape {
+    int64_t l, m, n, p, k, n2;
+} pp_shape;
+
+/* Options; pass NULL for the defaults shown. */
+typedef struct pp_opts {
+    int32_t max_sweeps;   /* Jacobi sweep cap (default 30)                         */
+    int32_t check_q;      /* nonzero: device check max|Q^T Q - I| <= q_tol (def 0)  */
+    float q_tol;          /* orthonormality tolerance (default 1e-5)                */
+    int32_t check_finite; /* nonzero: device scan of A for NaN/Inf (default 0)      */
+    float jacobi_tol;     /* rotation threshold on |cos| (0 = sqrt(len) * 2^-24)    */
+    int32_t reserved[4];
+} pp_opts;
+
+/* Device-written report of a decomposition call (all sums in FP64). */
+typedef struct pp_report {
+    int32_t status;       /* PP_OK or a device-detected pp_status                  */
+    int32_t sweeps;       /* largest Jacobi sweep count over the p slices          */
+    int64_t K;            /* Alg. 4.2 energy index (0 for tsvdq_trunc)             */
+    int64_t kappa;        /* implicit rank sum_i rho_i (Def. 4.4); k*p for trunc    */
+    double normA2;        /* |A|_F^2                                               */
+    double normAh2;       /* |A x_3 Q^T|_F^2, the transform-domain energy           */
+    double kept2;         /* sum of retained sigma^2                               */
+    double discarded2;    /* sum of discarded sigma^2 (Eckart-Young term, Thm 4.2) */
+    double err2;          /* |A - A_k|_F^2 computed from A_k (only if computed)     */
+    double proj_err2;     /* |A|^2 - |A x_3 Q^T|^2: projection error of Thm 4.2,    */
+                          /* exact only for orthonormal Q; suffers cancellation    */
+} pp_report;
+
+/* Human-readable name of a status code (static string). */
+PP_API const char *pp_status_str(int32_t status);
+
+/* Library version string, e.g. "pprod-gb300 0.1 sm_103a". */
+PP_API const char *pp_version(void);
+
+/* Workspace bytes needed by `op` at `shape` (0 if none).  Returns 0 and sets
+ * nothing for invalid shapes; the entry point itself reports the error. */
+PP_API size_t pp_workspace_bytes(int32_t op, const pp_shape *shape);
+
+/*
+ * Mode-3 product with Q or Q^T (Def. 2.2; the transform and reverse
+ * transform of Def. 3.1 / Alg. 4.1 steps 2 and 4).
+ *   transpose == 0:  Y = X x_3 Q^T   X is l x m x n, Y is l x m x p
+ *   transpose == 1:  Y = X x_3 Q     X is l x m x p, Y is l x m x n
+ * i.e. Y(i,j,t) = sum_s M(t,s) X(i,j,s) with M = Q^T or Q.  FP32 in/out,
+ * FP32 accumulation in the 3-pass split-TF32 tensor-core path.  No workspace.
+ */
+PP_API pp_status pprod_mode3(const float *X, int64_t l, int64_t m, int64_t n,
+                      const float *Q, int64_t p, int32_t transpose, float *Y,
+                      void *stream);
+
+/*
+ * Facewise product (Def. 2.3): Ch(:,:,t) = Ah(:,:,t) Bh(:,:,t), t < p.
+ * Ah is n1 x m x p, Bh is m x n2 x p, Ch is n1 x n2 x p.  No workspace.
+ */
+PP_API pp_status pprod_facewise(const float *Ah, const float *Bh, int64_t n1, int64_t m,
+                         int64_t n2, int64_t p, float *Ch, void *stream);
+
+/*
+ * Projected product (Def. 3.1): C = [(A x_3 Q^T) ^ (B x_3 Q^T)] x_3 Q.
+ * A is n1 x m x n, B is m x n2 x n, Q is n x p, C is n1 x n2 x n.
+ * Workspace: pp_workspace_bytes(PP_OP_PPROD, {l=n1, m=m, n=n, p=p, n2=n2}).
+ */
+PP_API pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1,
+                int64_t m, int64_t n2, int64_t n, int64_t p, float *C,
+                void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Truncated *Q-SVD (Alg. 4.1; Def. 4.1; error terms of Thm. 4.2).
+ *   A is l x m x n, Q is n x p (1 <= p <= n), 1 <= k <= min(l, m).
+ * Outputs (transform-domain factors: the storage counted in Sec. 5.1.2):
+ *   Uh  p x l x k  -- slice t is U-hat_k(:,:,t), row-major l x k
+ *   s   p x k      -- singular values of slice t, descending
+ *   Vh  p x m x k  -- slice t is V-hat_k(:,:,t), row-major m x k
+ *   Ak  n x l x m  -- A_k = (U-hat_k S-hat_k V-hat_k^T) x_3 Q; may be NULL,
+ *                     then A_k is formed in the workspace for rep->err2
+ *   rep            -- device pointer, may be NULL
+ * For a singular value that is exactly zero the matching short-side vector
+ * is returned as zero.  Workspace: pp_workspace_bytes(PP_OP_TSVDQ, ...).
+ */
+PP_API pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m,
+                      int64_t n, int64_t p, int64_t k, float *Uh, float *s,
+                      float *Vh, float *Ak, pp_report *rep, const pp_opts *opts,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * *Q-SVDII (Alg. 4.2; Defs. 4.3-4.4; error terms of Thm. 4.4).
+ *   A is l x m x n, Q is n x p, gamma in (0, 1].
+ * All p*min(l,m) squared singular values are ordered globally (descending
+ * sigma^2; ties by slice, then by index within the slice), K is the first
+ * index whose cumulative energy reaches gamma * |A x_3 Q^T|^2 (the energy is
+ * summed in FP64 from the FP32 singular values), and rho_t counts slice t's
+ * values among the first K (K = 0 and rho = 0 when the energy is zero).
+ * Outputs:
+ *   rho     int32  p       per-slice ranks (the *Q-multirank kept)
+ *   offs    int64  p+1     offs[t] = sum_{t'<t} rho_t', offs[p] = kappa
+ *   Uh_pk   float  capacity p*min(l,m)*l: slice t's l x rho_t block
+ *                  (row-major) starts at l*offs[t]
+ *   s_pk    float  capacity p*min(l,m): slice t's rho_t values at offs[t]
+ *   Vh_pk   float  capacity p*min(l,m)*m: slice t's m x rho_t block at m*offs[t]
+ *   Ak      float  n x l x m (may be NULL), rep (device, may be NULL)
+ * Workspace: pp_workspace_bytes(PP_OP_TSVDQII, ...).
+ */
+PP_API pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m,
+                  int64_t n, int64_t p, double gamma, int32_t *rho,
+                  int64_t *offs, float *Uh_pk, float *s_pk, float *Vh_pk,
+                  float *Ak, pp_report *rep, const pp_opts *opts, void *ws,
+                  size_t ws_bytes, void *stream);
+
+/*
+ * Instrumentation for benchmarks (no counterpart in the paper).
+ *
+ * pp_set_stage_events: register up to 8 caller-created CUDA events
+ * (cudaEvent_t passed as void*; NULL/0 disables).  While registered,
+ * tsvdq_trunc and tsvdqII record events[i] on their stream at stage
+ * boundaries: 0 entry, 1 after the projection and energies, 2 after the
+ * facewise Jacobi SVD, 3 after the global select (tsvdqII; repeated for
+ * tsvdq_trunc), 4 after factors and rebuild, 5 after the back-projection and
+ * report.  Process-wide state: not for concurrent use from several threads.
+ *
+ * pp_kernel_launches: number of kernels this library has launched so far in
+ * the process (monotone counter).
+ */
+PP_API void pp_set_stage_events(void *const *events, int32_t n);
+PP_API uint64_t pp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPROD_H */

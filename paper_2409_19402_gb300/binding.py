@@ -1,0 +1,275 @@
+"""Thin ctypes binding of the C ABI in include/pprod.h (same names).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``libpprod.so``.  PyTorch supplies device memory (outputs and the
+workspace are allocated here, by the caller side of the ABI) and the current
+CUDA stream.  There is no CPU fallback: if the library is missing or a CUDA
+device is absent the calls raise.
+
+Tensors follow the library's layout: an l x m x n tensor is a C-contiguous
+FP32 CUDA tensor of shape (n, l, m); Q is (n, p).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpprod.so")
+
+PP_OK, PP_EINVAL, PP_ESHAPE, PP_ENOTORTHO, PP_ENONFINITE, PP_ENOCONV = 0, 1, 2, 3, 4, 5
+PP_ETIMEOUT, PP_EWORKSPACE, PP_ECUDA, PP_ENOSYS = 6, 7, 8, 9
+PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII = 0, 1, 2, 3, 4
+
+
+class PPError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)}")
+        self.status = status
+
+
+class pp_shape(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("l", "m", "n", "p", "k", "n2")]
+
+
+class pp_opts(ctypes.Structure):
+    _fields_ = [("max_sweeps", ctypes.c_int32), ("check_q", ctypes.c_int32),
+                ("q_tol", ctypes.c_float), ("check_finite", ctypes.c_int32),
+                ("jacobi_tol", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+
+
+class pp_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("K", ctypes.c_int64),
+                ("kappa", ctypes.c_int64), ("normA2", ctypes.c_double),
+                ("normAh2", ctypes.c_double), ("kept2", ctypes.c_double),
+                ("discarded2", ctypes.c_double), ("err2", ctypes.c_double),
+                ("proj_err2", ctypes.c_double)]
+
+
+REPORT_BYTES = ctypes.sizeof(pp_report)
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libpprod.so (built by __graft_entry__.build()); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+        L.pp_status_str.argtypes = [i32]
+        L.pp_status_str.restype = ctypes.c_char_p
+        L.pp_version.restype = ctypes.c_char_p
+        L.pp_workspace_bytes.argtypes = [i32, ctypes.POINTER(pp_shape)]
+        L.pp_workspace_bytes.restype = sz
+        L.pprod_mode3.argtypes = [vp, i64, i64, i64, vp, i64, i32, vp, vp]
+        L.pprod_facewise.argtypes = [vp, vp, i64, i64, i64, i64, vp, vp]
+        L.pprod.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, vp, vp, sz, vp]
+        L.tsvdq_trunc.argtypes = [vp, vp, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp,
+                                  ctypes.POINTER(pp_opts), vp, sz, vp]
+        L.tsvdqII.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp, vp, vp,
+                              vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
+        for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII"):
+            getattr(L, f).restype = i32
+        L.pp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
+        L.pp_set_stage_events.restype = None
+        L.pp_kernel_launches.restype = ctypes.c_uint64
+        _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    return lib().pp_status_str(int(status)).decode()
+
+
+def version() -> str:
+    return lib().pp_version().decode()
+
+
+def kernel_launches() -> int:
+    """Process-wide count of kernels launched by libpprod.so."""
+    return int(lib().pp_kernel_launches())
+
+
+def set_stage_events(events) -> None:
+    """Register torch.cuda.Event objects (already recorded once, so that they
+    exist) as stage-boundary events of tsvdq_trunc / tsvdqII; None clears."""
+    if not events:
+        lib().pp_set_stage_events(None, 0)
+        return
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    lib().pp_set_stage_events(arr, len(events))
+
+
+def workspace_bytes(op: int, l=0, m=0, n=0, p=0, k=0, n2=0) -> int:
+    sh = pp_shape(l, m, n, p, k, n2)
+    return int(lib().pp_workspace_bytes(op, ctypes.byref(sh)))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check_t(t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+
+
+def _raise(st: int, what: str):
+    if st != PP_OK:
+        raise PPError(st, what)
+
+
+def _opts(max_sweeps=0, check_q=False, q_tol=0.0, check_finite=False, jacobi_tol=0.0):
+    return pp_opts(int(max_sweeps), int(bool(check_q)), float(q_tol), int(bool(check_finite)),
+                   float(jacobi_tol))
+
+
+def workspace(nbytes: int, device) -> torch.Tensor | None:
+    return None if nbytes == 0 else torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def read_report(rep: torch.Tensor) -> pp_report:
+    """Copy a device pp_report (uint8 tensor) to the host and unpack it."""
+    raw = bytes(rep.cpu().numpy().tobytes())
+    return pp_report.from_buffer_copy(raw)
+
+
+# --------------------------------------------------------------- entry points
+def pprod_mode3(X: torch.Tensor, Q: torch.Tensor, transpose: int, out=None, stream=None):
+    """Def. 2.2: transpose=0 -> X x_3 Q^T (n -> p slices); 1 -> X x_3 Q (p -> n)."""
+    _check_t(X, "X"); _check_t(Q, "Q")
+    n, p = Q.shape
+    s_in, l, m = X.shape
+    if s_in != (n if transpose == 0 else p):
+        raise ValueError("X slice count does not match Q")
+    if out is None:
+        out = torch.empty(((p if transpose == 0 else n), l, m), dtype=torch.float32,
+                          device=X.device)
+    _raise(lib().pprod_mode3(_ptr(X), l, m, n, _ptr(Q), p, int(transpose), _ptr(out),
+                             _stream(stream)), "pprod_mode3")
+    return out
+
+
+def pprod_facewise(Ah: torch.Tensor, Bh: torch.Tensor, out=None, stream=None):
+    """Def. 2.3: Ch[t] = Ah[t] @ Bh[t]."""
+    _check_t(Ah, "Ah"); _check_t(Bh, "Bh")
+    p, n1, m = Ah.shape
+    n2 = Bh.shape[2]
+    if out is None:
+        out = torch.empty((p, n1, n2), dtype=torch.float32, device=Ah.device)
+    _raise(lib().pprod_facewise(_ptr(Ah), _ptr(Bh), n1, m, n2, p, _ptr(out), _stream(stream)),
+           "pprod_facewise")
+    return out
+
+
+def pprod(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, out=None, ws=None, stream=None):
+    """Def. 3.1: A *Q B."""
+    _check_t(A, "A"); _check_t(B, "B"); _check_t(Q, "Q")
+    n, n1, m = A.shape
+    n2 = B.shape[2]
+    p = Q.shape[1]
+    if out is None:
+        out = torch.empty((n, n1, n2), dtype=torch.float32, device=A.device)
+    need = workspace_bytes(PP_OP_PPROD, l=n1, m=m, n=n, p=p, n2=n2)
+    if ws is None:
+        ws = workspace(need, A.device)
+    _raise(lib().pprod(_ptr(A), _ptr(B), _ptr(Q), n1, m, n2, n, p, _ptr(out), _ptr(ws),
+                       0 if ws is None else ws.numel(), _stream(stream)), "pprod")
+    return out
+
+
+@dataclass
+class TsvdqOut:
+    Uh: torch.Tensor     # (p, l, k)
+    s: torch.Tensor      # (p, k)
+    Vh: torch.Tensor     # (p, m, k)
+    Ak: torch.Tensor | None
+    rep: torch.Tensor    # device pp_report bytes
+
+    def report(self) -> pp_report:
+        return read_report(self.rep)
+
+
+def tsvdq_trunc(A: torch.Tensor, Q: torch.Tensor, k: int, want_ak: bool = True, ws=None,
+                stream=None, **opts) -> TsvdqOut:
+    """Alg. 4.1 truncated *Q-SVD."""
+    _check_t(A, "A"); _check_t(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    dev = A.device
+    Uh = torch.empty((p, l, k), dtype=torch.float32, device=dev)
+    s = torch.empty((p, k), dtype=torch.float32, device=dev)
+    Vh = torch.empty((p, m, k), dtype=torch.float32, device=dev)
+    Ak = torch.empty((n, l, m), dtype=torch.float32, device=dev) if want_ak else None
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_TSVDQ, l=l, m=m, n=n, p=p, k=k)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().tsvdq_trunc(_ptr(A), _ptr(Q), l, m, n, p, int(k), _ptr(Uh), _ptr(s), _ptr(Vh),
+                             _ptr(Ak), _ptr(rep), ctypes.byref(o), _ptr(ws),
+                             0 if ws is None else ws.numel(), _stream(stream)), "tsvdq_trunc")
+    return TsvdqOut(Uh, s, Vh, Ak, rep)
+
+
+@dataclass
+class TsvdqIIOut:
+    rho: torch.Tensor    # (p,) int32
+    offs: torch.Tensor   # (p+1,) int64
+    Uh: torch.Tensor     # packed, capacity p*r*l
+    s: torch.Tensor      # packed, capacity p*r
+    Vh: torch.Tensor     # packed, capacity p*r*m
+    Ak: torch.Tensor | None
+    rep: torch.Tensor
+    l: int
+    m: int
+
+    def report(self) -> pp_report:
+        return read_report(self.rep)
+
+    def slices(self):
+        """Per-slice host copies [(Uh_t (l, rho_t), s_t, Vh_t (m, rho_t)), ...]."""
+        rho = self.rho.cpu().tolist()
+        offs = self.offs.cpu().tolist()
+        U, S, V = self.Uh.cpu(), self.s.cpu(), self.Vh.cpu()
+        out = []
+        for t, r in enumerate(rho):
+            o = offs[t]
+            out.append((U[self.l * o: self.l * o + self.l * r].reshape(self.l, r),
+                        S[o: o + r], V[self.m * o: self.m * o + self.m * r].reshape(self.m, r)))
+        return out
+
+
+def tsvdqII(A: torch.Tensor, Q: torch.Tensor, gamma: float, want_ak: bool = True, ws=None,
+            stream=None, **opts) -> TsvdqIIOut:
+    """Alg. 4.2 *Q-SVDII."""
+    _check_t(A, "A"); _check_t(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    r = min(l, m)
+    dev = A.device
+    rho = torch.empty(p, dtype=torch.int32, device=dev)
+    offs = torch.empty(p + 1, dtype=torch.int64, device=dev)
+    Uh = torch.empty(p * r * l, dtype=torch.float32, device=dev)
+    s = torch.empty(p * r, dtype=torch.float32, device=dev)
+    Vh = torch.empty(p * r * m, dtype=torch.float32, device=dev)
+    Ak = torch.empty((n, l, m), dtype=torch.float32, device=dev) if want_ak else None
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_TSVDQII, l=l, m=m, n=n, p=p)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().tsvdqII(_ptr(A), _ptr(Q), l, m, n, p, float(gamma), _ptr(rho), _ptr(offs),
+                         _ptr(Uh), _ptr(s), _ptr(Vh), _ptr(Ak), _ptr(rep), ctypes.byref(o),
+                         _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)), "tsvdqII")
+    return TsvdqIIOut(rho, offs, Uh, s, Vh, Ak, rep, l, m)

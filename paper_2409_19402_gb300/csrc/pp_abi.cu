@@ -1,0 +1,402 @@
+// pp_abi.cu -- the extern "C" entry points declared in include/pprod.h:
+// argument validation, workspace carving and the stream-ordered launch
+// sequence of each operation.  No entry point allocates, frees, copies to or
+// from the host, or synchronises.
+#include <string.h>
+
+#include <atomic>
+
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace pp
+
+namespace {
+
+// benchmark stage events (see pp_set_stage_events)
+cudaEvent_t g_events[8];
+int g_nevents = 0;
+
+void stage(int i, cudaStream_t st) {
+  if (i < g_nevents && g_events[i]) cudaEventRecord(g_events[i], st);
+}
+
+using pp::round_up;
+
+// Bump allocator over the caller's workspace; with base == nullptr it only
+// measures (used by pp_workspace_bytes).
+struct Carve {
+  char *base;
+  size_t off = 0;
+  explicit Carve(void *b) : base(static_cast<char *>(b)) {}
+  template <class T>
+  T *take(int64_t count) {
+    off = (size_t)round_up((int64_t)off, 256);
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off += (size_t)count * sizeof(T);
+    return p;
+  }
+};
+
+constexpr int64_t MAX_LONG_SIDE = 768;   // longest slice side the Jacobi kernel is built for
+
+struct DecompWs {
+  float *Ah, *W, *sig, *Ahk;
+  int32_t *perm, *sweeps, *status, *rank;
+  double *kept_p, *disc_p, *part_a, *part_h, *part_e, *scal, *keys;
+  int64_t *K;
+};
+
+DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool ragged) {
+  const int64_t b = l < m ? l : m;
+  const int64_t a_pad = pp::jacobi_apad(l, m);
+  DecompWs w{};
+  w.Ah = c.take<float>(p * l * m);
+  w.W = c.take<float>(p * b * a_pad);
+  w.sig = c.take<float>(p * b);
+  w.perm = c.take<int32_t>(p * b);
+  w.sweeps = c.take<int32_t>(p);
+  w.Ahk = c.take<float>(p * l * m);
+  w.kept_p = c.take<double>(p);
+  w.disc_p = c.take<double>(p);
+  w.part_a = c.take<double>(pp::sumsq_max_partials());
+  w.part_h = c.take<double>(pp::sumsq_max_partials());
+  w.part_e = c.take<double>(pp::mode3_gemm_max_partials(n, l * m));
+  w.scal = c.take<double>(8);
+  w.status = c.take<int32_t>(1);
+  w.K = c.take<int64_t>(1);
+  if (ragged) {
+    w.keys = c.take<double>(p * b);
+    w.rank = c.take<int32_t>(p * b);
+  }
+  return w;
+}
+
+pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUDA; }
+
+#define PP_TRY(expr)                            \
+  do {                                          \
+    cudaError_t _e = (expr);                    \
+    if (_e != cudaSuccess) return PP_ECUDA;     \
+  } while (0)
+
+pp_status check_ws(const void *ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return PP_OK;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need) return PP_EWORKSPACE;
+  return PP_OK;
+}
+
+struct Opts {
+  int32_t max_sweeps = 30;
+  int32_t check_q = 0;
+  float q_tol = 1e-5f;
+  int32_t check_finite = 0;
+  float jacobi_tol = 0.f;
+};
+
+Opts read_opts(const pp_opts *o) {
+  Opts r;
+  if (o) {
+    if (o->max_sweeps > 0) r.max_sweeps = o->max_sweeps;
+    r.check_q = o->check_q;
+    if (o->q_tol > 0.f) r.q_tol = o->q_tol;
+    r.check_finite = o->check_finite;
+    r.jacobi_tol = o->jacobi_tol;
+  }
+  return r;
+}
+
+float default_tol(int64_t l, int64_t m) {
+  const double a = (double)(l > m ? l : m);
+  return (float)(sqrt(a) * 5.9604644775390625e-08);   // sqrt(a) * 2^-24
+}
+
+// Steps shared by Alg. 4.1 and Alg. 4.2 up to the facewise SVD.
+pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                          int64_t p, const Opts &o, const DecompWs &w, cudaStream_t st) {
+  PP_TRY(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+  if (o.check_q) PP_TRY(pp::launch_check_q(Q, n, p, o.q_tol, w.status, st));
+  if (o.check_finite) PP_TRY(pp::launch_check_finite(A, n * l * m, w.status, st));
+  // Alg. 4.1 step 2: A-hat = A x_3 Q^T;  M(r, c) = Q^T(r, c) = Q[c*p + r]
+  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, nullptr, st));
+  int np = 0;
+  PP_TRY(pp::launch_sumsq(A, n * l * m, w.part_a, &np, st));
+  PP_TRY(pp::launch_sum_partials(w.part_a, np, w.scal + 0, st));
+  PP_TRY(pp::launch_sumsq(w.Ah, p * l * m, w.part_h, &np, st));
+  PP_TRY(pp::launch_sum_partials(w.part_h, np, w.scal + 1, st));
+  stage(1, st);
+  // step 3: facewise SVD
+  pp::JacobiArgs ja;
+  ja.X = w.Ah;
+  ja.W = w.W;
+  ja.sig = w.sig;
+  ja.perm = w.perm;
+  ja.sweeps = w.sweeps;
+  ja.status = w.status;
+  ja.l = l;
+  ja.m = m;
+  ja.p = p;
+  ja.max_sweeps = o.max_sweeps;
+  ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(l, m);
+  PP_TRY(pp::launch_jacobi(ja, st));
+  stage(2, st);
+  return PP_OK;
+}
+
+// Back-projection A_k = A-hat_k x_3 Q with the fused error |A - A_k|^2.
+pp_status backproject(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                      int64_t p, float *Ak, const DecompWs &w, cudaStream_t st) {
+  int np = 0;
+  // M(r, c) = Q(r, c) = Q[r*p + c]
+  PP_TRY(pp::launch_mode3_gemm(Q, p, 1, w.Ahk, Ak, n, p, l * m, A, w.part_e, &np, st));
+  PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 2, st));
+  return PP_OK;
+}
+
+bool bad_dims(int64_t l, int64_t m, int64_t n, int64_t p) {
+  return l < 1 || m < 1 || n < 1 || p < 1 || p > n || l > (1 << 20) || m > (1 << 20) ||
+         n > (1 << 20) || l * m > (int64_t)1 << 31;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pp_status_str(int32_t s) {
+  switch (s) {
+    case PP_OK: return "PP_OK";
+    case PP_EINVAL: return "PP_EINVAL: invalid argument";
+    case PP_ESHAPE: return "PP_ESHAPE: invalid or unsupported sizes";
+    case PP_ENOTORTHO: return "PP_ENOTORTHO: Q does not have orthonormal columns";
+    case PP_ENONFINITE: return "PP_ENONFINITE: non-finite input";
+    case PP_ENOCONV: return "PP_ENOCONV: Jacobi SVD did not converge within max_sweeps";
+    case PP_ETIMEOUT: return "PP_ETIMEOUT: bounded device wait expired";
+    case PP_EWORKSPACE: return "PP_EWORKSPACE: workspace missing, misaligned or too small";
+    case PP_ECUDA: return "PP_ECUDA: CUDA launch or runtime error";
+    case PP_ENOSYS: return "PP_ENOSYS: variant not built";
+    default: return "unknown pp_status";
+  }
+}
+
+const char *pp_version(void) { return "pprod-gb300 0.1 sm_103a"; }
+
+void pp_set_stage_events(void *const *events, int32_t n) {
+  if (!events || n <= 0) {
+    g_nevents = 0;
+    return;
+  }
+  if (n > 8) n = 8;
+  for (int i = 0; i < n; ++i) g_events[i] = static_cast<cudaEvent_t>(events[i]);
+  g_nevents = n;
+}
+
+uint64_t pp_kernel_launches(void) { return pp::g_launches.load(); }
+
+size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
+  if (!sh) return 0;
+  Carve c(nullptr);
+  switch (op) {
+    case PP_OP_MODE3:
+    case PP_OP_FACEWISE:
+      return 0;
+    case PP_OP_PPROD:
+      if (sh->l < 1 || sh->m < 1 || sh->n2 < 1 || sh->p < 1) return 0;
+      c.take<float>(sh->p * sh->l * sh->m);
+      c.take<float>(sh->p * sh->m * sh->n2);
+      c.take<float>(sh->p * sh->l * sh->n2);
+      return c.off;
+    case PP_OP_TSVDQ:
+    case PP_OP_TSVDQII:
+      if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
+      carve_decomp(c, sh->l, sh->m, sh->n, sh->p, op == PP_OP_TSVDQII);
+      return c.off;
+    default:
+      return 0;
+  }
+}
+
+pp_status pprod_mode3(const float *X, int64_t l, int64_t m, int64_t n, const float *Q, int64_t p,
+                      int32_t transpose, float *Y, void *stream) {
+  if (!X || !Q || !Y) return PP_EINVAL;
+  if (transpose != 0 && transpose != 1) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (transpose == 0)   // Y (p slices) = X (n slices) x_3 Q^T
+    return cuda_status(pp::launch_mode3_gemm(Q, 1, p, X, Y, p, n, l * m, nullptr, nullptr,
+                                             nullptr, st));
+  // Y (n slices) = X (p slices) x_3 Q
+  return cuda_status(pp::launch_mode3_gemm(Q, p, 1, X, Y, n, p, l * m, nullptr, nullptr,
+                                           nullptr, st));
+}
+
+pp_status pprod_facewise(const float *Ah, const float *Bh, int64_t n1, int64_t m, int64_t n2,
+                         int64_t p, float *Ch, void *stream) {
+  if (!Ah || !Bh || !Ch) return PP_EINVAL;
+  if (n1 < 1 || m < 1 || n2 < 1 || p < 1 || p > 65535 || n1 > (1 << 20) || n2 > (1 << 20))
+    return PP_ESHAPE;
+  return cuda_status(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p,
+                                              static_cast<cudaStream_t>(stream)));
+}
+
+pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1, int64_t m,
+                int64_t n2, int64_t n, int64_t p, float *C, void *ws, size_t ws_bytes,
+                void *stream) {
+  if (!A || !B || !Q || !C) return PP_EINVAL;
+  if (bad_dims(n1, m, n, p) || bad_dims(m, n2, n, p) || bad_dims(n1, n2, n, p) || p > 65535)
+    return PP_ESHAPE;
+  pp_shape sh{n1, m, n, p, 0, n2};
+  const size_t need = pp_workspace_bytes(PP_OP_PPROD, &sh);
+  if (pp_status s = check_ws(ws, ws_bytes, need)) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  float *Ah = c.take<float>(p * n1 * m);
+  float *Bh = c.take<float>(p * m * n2);
+  float *Ch = c.take<float>(p * n1 * n2);
+  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, Ah, p, n, n1 * m, nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, B, Bh, p, n, m * n2, nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st));
+  PP_TRY(pp::launch_mode3_gemm(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, st));
+  return PP_OK;
+}
+
+pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m, int64_t n, int64_t p,
+                      int64_t k, float *Uh, float *s, float *Vh, float *Ak, pp_report *rep,
+                      const pp_opts *opts, void *ws, size_t ws_bytes, void *stream) {
+  if (!A || !Q || !Uh || !s || !Vh) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  const int64_t b = l < m ? l : m;
+  if (k < 1 || k > b) return PP_ESHAPE;
+  if ((l > m ? l : m) > MAX_LONG_SIDE) return PP_ENOSYS;
+  pp_shape sh{l, m, n, p, k, 0};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_TSVDQ, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const DecompWs w = carve_decomp(c, l, m, n, p, false);
+  stage(0, st);
+  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  stage(3, st);
+  pp::FactorArgs fa;
+  fa.X = w.Ah;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = l;
+  fa.m = m;
+  fa.p = p;
+  fa.b = b;
+  fa.a_pad = pp::jacobi_apad(l, m);
+  fa.kfix = k;
+  fa.rho = nullptr;
+  fa.offs = nullptr;
+  fa.Uh = Uh;
+  fa.s = s;
+  fa.Vh = Vh;
+  fa.Ahk = w.Ahk;
+  fa.kept_partial = w.kept_p;
+  fa.disc_partial = w.disc_p;
+  PP_TRY(pp::launch_factors(fa, st));
+  stage(4, st);
+  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st)) return e;
+  if (rep) {
+    pp::ReportArgs ra;
+    ra.rep = rep;
+    ra.status = w.status;
+    ra.sweeps = w.sweeps;
+    ra.p = p;
+    ra.normA2 = w.scal + 0;
+    ra.normAh2 = w.scal + 1;
+    ra.err2 = w.scal + 2;
+    ra.kept_partial = w.kept_p;
+    ra.disc_partial = w.disc_p;
+    ra.sel_scal = nullptr;
+    ra.K = nullptr;
+    ra.kappa_fixed = k * p;
+    ra.offs = nullptr;
+    PP_TRY(pp::launch_report(ra, st));
+  }
+  stage(5, st);
+  return PP_OK;
+}
+
+pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t n, int64_t p,
+                  double gamma, int32_t *rho, int64_t *offs, float *Uh_pk, float *s_pk,
+                  float *Vh_pk, float *Ak, pp_report *rep, const pp_opts *opts, void *ws,
+                  size_t ws_bytes, void *stream) {
+  if (!A || !Q || !rho || !offs || !Uh_pk || !s_pk || !Vh_pk) return PP_EINVAL;
+  if (!(gamma > 0.0 && gamma <= 1.0)) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  const int64_t b = l < m ? l : m;
+  if ((l > m ? l : m) > MAX_LONG_SIDE) return PP_ENOSYS;
+  if (p * b > ((int64_t)1 << 31) - 1) return PP_ESHAPE;
+  pp_shape sh{l, m, n, p, 0, 0};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_TSVDQII, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const DecompWs w = carve_decomp(c, l, m, n, p, true);
+  stage(0, st);
+  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  // Alg. 4.2 steps 4-7
+  pp::SelectArgs sa;
+  sa.sig = w.sig;
+  sa.p = p;
+  sa.b = b;
+  sa.gamma = gamma;
+  sa.keys_sorted = w.keys;
+  sa.rank = w.rank;
+  sa.rho = rho;
+  sa.offs = offs;
+  sa.scal = w.scal + 4;
+  sa.K = w.K;
+  PP_TRY(pp::launch_select(sa, st));
+  stage(3, st);
+  // step 8: truncated factors (packed) and the rebuild
+  pp::FactorArgs fa;
+  fa.X = w.Ah;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = l;
+  fa.m = m;
+  fa.p = p;
+  fa.b = b;
+  fa.a_pad = pp::jacobi_apad(l, m);
+  fa.kfix = 0;
+  fa.rho = rho;
+  fa.offs = offs;
+  fa.Uh = Uh_pk;
+  fa.s = s_pk;
+  fa.Vh = Vh_pk;
+  fa.Ahk = w.Ahk;
+  fa.kept_partial = nullptr;
+  fa.disc_partial = nullptr;
+  PP_TRY(pp::launch_factors(fa, st));
+  stage(4, st);
+  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st)) return e;
+  if (rep) {
+    pp::ReportArgs ra;
+    ra.rep = rep;
+    ra.status = w.status;
+    ra.sweeps = w.sweeps;
+    ra.p = p;
+    ra.normA2 = w.scal + 0;
+    ra.normAh2 = w.scal + 1;
+    ra.err2 = w.scal + 2;
+    ra.kept_partial = nullptr;
+    ra.disc_partial = nullptr;
+    ra.sel_scal = w.scal + 4;
+    ra.K = w.K;
+    ra.kappa_fixed = -1;
+    ra.offs = offs;
+    PP_TRY(pp::launch_report(ra, st));
+  }
+  stage(5, st);
+  return PP_OK;
+}
+
+}  // extern "C"

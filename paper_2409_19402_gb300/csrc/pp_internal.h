@@ -1,0 +1,109 @@
+// pp_internal.h -- private declarations shared by the CUDA translation units
+// of the projected t-SVD library.  Not part of the public C ABI (pprod.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pprod.h"
+
+namespace pp {
+
+// Count `n` kernel launches in the process-wide counter (pp_kernel_launches).
+void count_launch(int n);
+
+// Round x up to a multiple of a.
+static inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Device-side error word: the first nonzero pp_status written wins.
+__device__ inline void set_status(int32_t *status, int32_t code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---------------------------------------------------------------- GEMMs
+// Y (P x N, row-major, ldY = N) = M (P x S) * X (S x N, row-major), with
+// M(r, c) = Qm[r * sr + c * sc].  When Aref != nullptr the launch also writes
+// sum (Aref - Y)^2 over each CTA tile to err_partials[CTA] (FP64); Y may then
+// be nullptr (error only).
+cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const float *X,
+                              float *Y, int64_t P, int64_t S, int64_t N, const float *Aref,
+                              double *err_partials, int *n_partials, cudaStream_t st);
+int64_t mode3_gemm_max_partials(int64_t P, int64_t N);
+
+// Batched facewise product C_t = A_t B_t (Def. 2.3).
+cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
+                                 int64_t m, int64_t n2, int64_t p, cudaStream_t st);
+
+// ---------------------------------------------------------------- Jacobi
+struct JacobiArgs {
+  const float *X;     // p faces, l x m row-major each (transform domain A-hat)
+  float *W;           // p * b * a_pad: rotated vectors (output / blocked store)
+  float *sig;         // p * b: singular values, descending per face
+  int32_t *perm;      // p * b: sorted position -> vector index
+  int32_t *sweeps;    // p: sweeps used per face
+  int32_t *status;    // device status word
+  int64_t l, m, p;
+  int32_t max_sweeps;
+  float tol;          // rotation threshold on |cos|
+};
+int64_t jacobi_apad(int64_t l, int64_t m);
+cudaError_t launch_jacobi(const JacobiArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- select (Alg. 4.2)
+struct SelectArgs {
+  const float *sig;        // p x b, descending per face
+  int64_t p, b;
+  double gamma;
+  double *keys_sorted;     // p*b, scratch
+  int32_t *rank;           // p*b, scratch: global position of (t, j)
+  int32_t *rho;            // p out
+  int64_t *offs;           // p+1 out
+  double *scal;            // scal[0] = kept2, scal[1] = total2, scal[2] = K (as double)
+  int64_t *K;              // out
+};
+cudaError_t launch_select(const SelectArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- factors / rebuild
+struct FactorArgs {
+  const float *X;          // A-hat, p faces l x m
+  const float *W;          // converged vectors, p * b * a_pad
+  const float *sig;        // p * b sorted
+  const int32_t *perm;     // p * b
+  int64_t l, m, p, b, a_pad;
+  int64_t kfix;            // fixed rank (tsvdq) or 0 -> ragged from rho/offs
+  const int32_t *rho;      // ragged ranks (tsvdqII) or nullptr
+  const int64_t *offs;     // ragged offsets or nullptr
+  float *Uh, *s, *Vh;      // outputs (fixed: p x l x k etc.; ragged: packed)
+  float *Ahk;              // rebuilt transform-domain tensor p x l x m
+  double *kept_partial;    // per face kept sigma^2 (FP64) -> used for trunc report
+  double *disc_partial;    // per face discarded sigma^2
+};
+cudaError_t launch_factors(const FactorArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------- reductions
+// partials[blk] = sum of x^2 over a fixed grid; returns the number of partials.
+cudaError_t launch_sumsq(const float *x, int64_t n, double *partials, int *n_partials,
+                         cudaStream_t st);
+int64_t sumsq_max_partials();
+// out[0] = sum of partials[0..n) in a fixed order.
+cudaError_t launch_sum_partials(const double *partials, int n_partials, double *out,
+                                cudaStream_t st);
+cudaError_t launch_check_q(const float *Q, int64_t n, int64_t p, float tol, int32_t *status,
+                           cudaStream_t st);
+cudaError_t launch_check_finite(const float *x, int64_t n, int32_t *status, cudaStream_t st);
+
+struct ReportArgs {
+  pp_report *rep;
+  const int32_t *status;
+  const int32_t *sweeps;
+  int64_t p;
+  const double *normA2, *normAh2, *err2;   // scalars (device)
+  const double *kept_partial, *disc_partial;  // per face (trunc) or nullptr
+  const double *sel_scal;                     // select scalars (tsvdqII) or nullptr
+  const int64_t *K;
+  int64_t kappa_fixed;                        // k*p for trunc, -1 for ragged (from offs)
+  const int64_t *offs;
+};
+cudaError_t launch_report(const ReportArgs &a, cudaStream_t st);
+
+}  // namespace pp

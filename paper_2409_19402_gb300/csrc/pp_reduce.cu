@@ -1,0 +1,138 @@
+// pp_reduce.cu -- FP64-accumulated reductions (energies of Thm. 4.2 / 4.4:
+// |A|_F^2 and |A-hat|_F^2), input checks (Q^T Q = I for Q in St_{n,p}, finite
+// input) and the device-written report.  Every reduction runs on a fixed grid
+// with a fixed combination order, so results are bitwise reproducible.
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double red[32];
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(RED_THREADS) sumsq_kernel(const float *__restrict__ x, int64_t n,
+                                                            double *__restrict__ partials) {
+  double acc = 0.0;
+  const int64_t n4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? n / 4 : 0;
+  const float4 *x4 = reinterpret_cast<const float4 *>(x);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = x4[i];
+    acc += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+  }
+  for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += (double)x[i] * x[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void sum_partials_kernel(const double *__restrict__ partials, int n,
+                                    double *__restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// max |(Q^T Q)_{ab} - delta_ab| > tol -> PP_ENOTORTHO; one thread per (a, b), b >= a
+__global__ void check_q_kernel(const float *__restrict__ Q, int64_t n, int64_t p, float tol,
+                               int32_t *status) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= p * p) return;
+  const int64_t a = idx / p, b = idx % p;
+  if (b < a) return;
+  double acc = 0.0;
+  for (int64_t s = 0; s < n; ++s) acc += (double)Q[s * p + a] * Q[s * p + b];
+  const double dev = fabs(acc - (a == b ? 1.0 : 0.0));
+  if (!(dev <= (double)tol)) set_status(status, PP_ENOTORTHO);
+}
+
+__global__ void check_finite_kernel(const float *__restrict__ x, int64_t n, int32_t *status) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(x[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, PP_ENONFINITE);
+}
+
+__global__ void report_kernel(ReportArgs a) {
+  if (threadIdx.x != 0) return;
+  pp_report r;
+  r.status = *a.status;
+  int32_t sw = 0;
+  for (int64_t t = 0; t < a.p; ++t) sw = max(sw, a.sweeps[t]);
+  r.sweeps = sw;
+  r.normA2 = *a.normA2;
+  r.normAh2 = *a.normAh2;
+  r.err2 = a.err2 ? *a.err2 : -1.0;
+  if (a.sel_scal) {
+    r.K = *a.K;
+    r.kappa = a.offs[a.p];
+    r.kept2 = a.sel_scal[0];
+    r.discarded2 = a.sel_scal[1] - a.sel_scal[0];
+  } else {
+    double kept = 0.0, disc = 0.0;
+    for (int64_t t = 0; t < a.p; ++t) { kept += a.kept_partial[t]; disc += a.disc_partial[t]; }
+    r.K = 0;
+    r.kappa = a.kappa_fixed;
+    r.kept2 = kept;
+    r.discarded2 = disc;
+  }
+  r.proj_err2 = r.normA2 - r.normAh2;
+  *a.rep = r;
+}
+
+}  // namespace
+
+int64_t sumsq_max_partials() { return RED_BLOCKS; }
+
+cudaError_t launch_sumsq(const float *x, int64_t n, double *partials, int *n_partials,
+                         cudaStream_t st) {
+  *n_partials = RED_BLOCKS;
+  count_launch(1);
+  sumsq_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, n, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_partials(const double *partials, int n_partials, double *out,
+                                cudaStream_t st) {
+  count_launch(1);
+  sum_partials_kernel<<<1, 1024, 0, st>>>(partials, n_partials, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_q(const float *Q, int64_t n, int64_t p, float tol, int32_t *status,
+                           cudaStream_t st) {
+  const int64_t total = p * p;
+  count_launch(1);
+  check_q_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(Q, n, p, tol, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(const float *x, int64_t n, int32_t *status, cudaStream_t st) {
+  count_launch(1);
+  check_finite_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, n, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_report(const ReportArgs &a, cudaStream_t st) {
+  count_launch(1);
+  report_kernel<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

@@ -1,0 +1,181 @@
+// pp_select.cu -- the global energy selection of the *Q-SVDII (Alg. 4.2,
+// steps 4-7): order all p*b squared singular values, find the first K whose
+// cumulative energy reaches gamma times the total, and count each slice's
+// members among the first K (rho_t).
+//
+// The order is the one the algorithm's permutation pi defines, made unique by
+// a tie rule: sigma^2 descending, then slice ascending, then position within
+// the slice ascending.  Each slice's values arrive sorted (descending), so
+// the global position of entry (t, j) is
+//   j + sum_{t' < t} #{sigma_{t'}^2 >= key} + sum_{t' > t} #{sigma_{t'}^2 > key},
+// computed with one binary search per other slice (a merge-path rank).  This
+// is exact and deterministic, unlike a histogram-based radix select whose
+// FP64 bucket sums would depend on atomic ordering.  Keys are sigma^2 formed
+// in FP64 from the FP32 sigma (exact: a 24-bit significand squared fits).
+//
+// The cumulative sums run in FP64 in one CTA: 1024 contiguous chunks summed
+// sequentially, a fixed-order scan of the chunk sums, then a second pass over
+// each chunk to find the first crossing.  The result is deterministic.
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int SEL_THREADS = 1024;
+
+__device__ __forceinline__ double key_of(const float *sig, int64_t idx) {
+  const double s = (double)sig[idx];
+  return s * s;
+}
+
+// number of entries of the descending row `row` (length b) with key' >= key (ge) or > key
+__device__ __forceinline__ int count_desc(const float *row, int b, double key, bool ge) {
+  int lo = 0, hi = b;   // first index where the predicate fails
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const double k2 = key_of(row, mid);
+    const bool in = ge ? (k2 >= key) : (k2 > key);
+    if (in) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void select_rank_kernel(const float *__restrict__ sig, int64_t p, int b,
+                                   double *__restrict__ keys_sorted, int32_t *__restrict__ rank,
+                                   int use_smem) {
+  extern __shared__ float ssig[];
+  const int64_t N = p * b;
+  const float *src = sig;
+  if (use_smem) {
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x) ssig[i] = sig[i];
+    __syncthreads();
+    src = ssig;
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / b;
+    const int j = (int)(e % b);
+    const double key = key_of(src, e);
+    int64_t pos = j;
+    for (int64_t t2 = 0; t2 < p; ++t2) {
+      if (t2 == t) continue;
+      pos += count_desc(src + t2 * b, b, key, t2 < t);
+    }
+    rank[e] = (int32_t)pos;
+    keys_sorted[pos] = key;
+  }
+}
+
+// Inclusive scan of v over the CTA in a fixed order (Hillis-Steele in shared memory).
+__device__ double block_inclusive_scan(double v, double *buf) {
+  const int tid = threadIdx.x;
+  buf[tid] = v;
+  __syncthreads();
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    const double add = tid >= off ? buf[tid - off] : 0.0;
+    __syncthreads();
+    buf[tid] += add;
+    __syncthreads();
+  }
+  const double r = buf[tid];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) select_finish_kernel(
+    const double *__restrict__ keys_sorted, const int32_t *__restrict__ rank, int64_t p, int b,
+    double gamma, int32_t *__restrict__ rho, int64_t *__restrict__ offs, double *__restrict__ scal,
+    int64_t *__restrict__ Kout) {
+  __shared__ double buf[SEL_THREADS];
+  __shared__ unsigned long long Ksh;
+  __shared__ double keptsh;
+  const int tid = threadIdx.x;
+  const int64_t N = p * b;
+  const int64_t chunk = (N + SEL_THREADS - 1) / SEL_THREADS;
+  const int64_t lo = tid * chunk, hi = min(N, lo + chunk);
+  double s = 0.0;
+  for (int64_t q = lo; q < hi; ++q) s += keys_sorted[q];
+  const double incl = block_inclusive_scan(s, buf);
+  // the exclusive prefix of a chunk is the previous thread's inclusive value
+  buf[tid] = incl;
+  if (tid == 0) { Ksh = 0xffffffffffffffffull; keptsh = 0.0; }
+  __syncthreads();
+  const double total = buf[SEL_THREADS - 1];
+  const double before = tid == 0 ? 0.0 : buf[tid - 1];
+  __syncthreads();
+  if (total > 0.0) {
+    const double thresh = gamma * total;
+    double c = before;
+    for (int64_t q = lo; q < hi; ++q) {
+      c += keys_sorted[q];
+      if (c >= thresh) {
+        atomicMin(&Ksh, (unsigned long long)(q + 1));
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  int64_t K = (total > 0.0) ? (int64_t)Ksh : 0;
+  if (total > 0.0 && Ksh == 0xffffffffffffffffull) K = N;   // unreachable for gamma <= 1
+  // kept energy c_K: the owning thread recomputes its running sum up to K
+  if (K > 0 && lo < K && K <= hi) {
+    double c = before;
+    for (int64_t q = lo; q < K; ++q) c += keys_sorted[q];
+    keptsh = c;
+  }
+  __syncthreads();
+  // per-slice ranks: rank[t*b + j] increases with j, count entries with rank < K
+  for (int64_t t = tid; t < p; t += SEL_THREADS) {
+    int lo2 = 0, hi2 = b;
+    while (lo2 < hi2) {
+      const int mid = (lo2 + hi2) >> 1;
+      if (rank[t * b + mid] < K) lo2 = mid + 1; else hi2 = mid;
+    }
+    rho[t] = lo2;
+  }
+  __syncthreads();
+  // offsets: exclusive scan of rho over p slices (chunked like the energies)
+  const int64_t pchunk = (p + SEL_THREADS - 1) / SEL_THREADS;
+  const int64_t plo = tid * pchunk, phi = min(p, plo + pchunk);
+  int64_t cnt = 0;
+  for (int64_t t = plo; t < phi; ++t) cnt += rho[t];
+  const double inc2 = block_inclusive_scan((double)cnt, buf);   // exact: integers < 2^53
+  int64_t run = (int64_t)inc2 - cnt;
+  for (int64_t t = plo; t < phi; ++t) {
+    offs[t] = run;
+    run += rho[t];
+  }
+  if (tid == SEL_THREADS - 1) offs[p] = (int64_t)inc2;
+  if (tid == 0) {
+    scal[0] = keptsh;
+    scal[1] = total;
+    *Kout = K;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_select(const SelectArgs &a, cudaStream_t st) {
+  const int64_t N = a.p * a.b;
+  const size_t smem_need = (size_t)N * sizeof(float);
+  const int use_smem = smem_need <= 160 * 1024;
+  int blocks = (int)((N + 255) / 256);
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  cudaError_t e;
+  if (use_smem) {
+    e = cudaFuncSetAttribute(select_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_need);
+    if (e != cudaSuccess) return e;
+  }
+  count_launch(1);
+  select_rank_kernel<<<blocks, 256, use_smem ? smem_need : 0, st>>>(
+      a.sig, a.p, (int)a.b, a.keys_sorted, a.rank, use_smem);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  count_launch(1);
+  select_finish_kernel<<<1, SEL_THREADS, 0, st>>>(a.keys_sorted, a.rank, a.p, (int)a.b,
+                                                  a.gamma, a.rho, a.offs, a.scal, a.K);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

@@ -1,0 +1,103 @@
+"""CPU-only checks of the C ABI: the library loads, exports every function
+declared in include/pprod.h, and rejects bad arguments on the host before any
+CUDA call is made (no GPU is touched here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from tests.conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "pprod.h")
+
+
+def _lib():
+    from paper_2409_19402_gb300 import binding
+    import __graft_entry__
+    if not os.path.exists(binding.LIB_PATH):
+        __graft_entry__.build()
+    return binding
+
+
+def declared_functions():
+    txt = open(HEADER).read()
+    return re.findall(r"PP_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt)
+
+
+def test_header_declares_the_entry_points():
+    names = set(declared_functions())
+    for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII",
+              "pp_workspace_bytes", "pp_status_str", "pp_version"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    b = _lib()
+    L = b.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_status_strings_and_version():
+    b = _lib()
+    assert b.status_str(0) == "PP_OK"
+    for s in range(1, 10):
+        assert b.status_str(s).startswith("PP_E")
+    assert "sm_103a" in b.version()
+
+
+def test_workspace_sizes():
+    b = _lib()
+    w1 = b.workspace_bytes(b.PP_OP_TSVDQ, l=120, m=160, n=300, p=50, k=5)
+    w2 = b.workspace_bytes(b.PP_OP_TSVDQII, l=120, m=160, n=300, p=50)
+    w3 = b.workspace_bytes(b.PP_OP_TSVDQII, l=120, m=160, n=300, p=300)
+    assert 0 < w1 <= w2 < w3
+    assert w2 >= 2 * 50 * 120 * 160 * 4            # A-hat and its rebuild at least
+    assert b.workspace_bytes(b.PP_OP_MODE3, l=4, m=4, n=4, p=2) == 0
+    assert b.workspace_bytes(b.PP_OP_TSVDQ, l=4, m=4, n=2, p=3) == 0   # p > n: invalid
+    assert b.workspace_bytes(b.PP_OP_PPROD, l=4, m=5, n=6, p=2, n2=3) >= 4 * (2 * 20 + 2 * 15 + 2 * 12)
+
+
+FAKE = ctypes.c_void_p(1 << 20)     # never dereferenced: the host rejects first
+
+
+def test_host_validation_codes():
+    b = _lib()
+    L = b.lib()
+    # NULL pointers -> PP_EINVAL
+    assert L.pprod_mode3(None, 4, 4, 4, None, 2, 0, None, None) == b.PP_EINVAL
+    # bad transpose flag
+    assert L.pprod_mode3(FAKE, 4, 4, 4, FAKE, 2, 7, FAKE, None) == b.PP_EINVAL
+    # p > n
+    assert L.pprod_mode3(FAKE, 4, 4, 4, FAKE, 5, 0, FAKE, None) == b.PP_ESHAPE
+    # k out of range
+    o = b.pp_opts()
+    for k in (0, 5):
+        assert L.tsvdq_trunc(FAKE, FAKE, 4, 6, 8, 2, k, FAKE, FAKE, FAKE, None, None,
+                             ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_ESHAPE
+    # workspace too small / misaligned / missing
+    assert L.tsvdq_trunc(FAKE, FAKE, 4, 6, 8, 2, 2, FAKE, FAKE, FAKE, None, None,
+                         ctypes.byref(o), FAKE, 16, None) == b.PP_EWORKSPACE
+    assert L.tsvdq_trunc(FAKE, FAKE, 4, 6, 8, 2, 2, FAKE, FAKE, FAKE, None, None,
+                         ctypes.byref(o), ctypes.c_void_p((1 << 20) + 4), 1 << 30,
+                         None) == b.PP_EWORKSPACE
+    assert L.tsvdq_trunc(FAKE, FAKE, 4, 6, 8, 2, 2, FAKE, FAKE, FAKE, None, None,
+                         ctypes.byref(o), None, 0, None) == b.PP_EWORKSPACE
+    # gamma outside (0, 1]
+    for g in (0.0, -0.5, 1.0000001, float("nan")):
+        assert L.tsvdqII(FAKE, FAKE, 4, 6, 8, 2, g, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                         ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_EINVAL
+    # slice longer than the Jacobi kernel is built for
+    assert L.tsvdqII(FAKE, FAKE, 4, 4096, 8, 2, 0.9, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                     ctypes.byref(o), FAKE, 1 << 40, None) == b.PP_ENOSYS
+    # facewise / pprod shapes
+    assert L.pprod_facewise(FAKE, FAKE, 0, 3, 3, 2, FAKE, None) == b.PP_ESHAPE
+    assert L.pprod(FAKE, FAKE, FAKE, 3, 3, 3, 4, 5, FAKE, FAKE, 1 << 20, None) == b.PP_ESHAPE
+
+
+def test_binding_refuses_cpu_tensors():
+    import torch
+    b = _lib()
+    with pytest.raises(ValueError):
+        b.pprod_mode3(torch.zeros(4, 2, 2), torch.zeros(4, 2), 0)

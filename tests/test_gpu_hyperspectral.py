@@ -1,0 +1,87 @@
+"""Hyperspectral-shaped config at full size (512 x 512 x 224, Q = U3 with
+p in {10, 100}, fixed k in {5, 20, 50}, gamma in {0.9, 0.99}).
+
+The FP64 oracle cannot decompose all slices in seconds at this size, so the
+checks are (a) sampled slices recomputed one by one by the oracle, and (b)
+properties that hold at any size: the error identity of Thm. 4.2/4.4, the
+bit-exact selection on the GPU's own singular values, A_k lying in range(Q).
+The 512-long slices exceed shared memory and run the block-cyclic Jacobi path.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2409_19402_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def data():
+    A = inputs.hyperspectral()
+    return A, {p: inputs.u3_q(A, p) for p in (10, 100)}
+
+
+def _b():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2409_19402_gb300 import binding
+    return binding
+
+
+def _slice_oracle(A, Q, t):
+    """A-hat(:,:,t) = A x_3 Q(:,t)^T computed by the oracle, then its SVD."""
+    Ah_t = oracle.mode3(A, np.asarray(Q, np.float64)[:, t:t + 1].T)[0]
+    U, s, V, _ = oracle.svd(Ah_t)
+    return Ah_t, U, s, V
+
+
+@pytest.mark.parametrize("p,k", [(10, 20), (100, 5)])
+def test_hyperspectral_tsvdq(data, p, k):
+    b = _b()
+    A, Qs = data
+    Q = Qs[p]
+    Ad, Qd = torch.from_numpy(A).cuda(), torch.from_numpy(Q).cuda()
+    out = b.tsvdq_trunc(Ad, Qd, k)
+    torch.cuda.synchronize()
+    rep = out.report()
+    assert rep.status == 0, b.status_str(rep.status)
+    # any-size property: Thm. 4.2 error identity (proj_err2 = |A|^2 - |A-hat|^2)
+    assert rep.err2 == pytest.approx(rep.discarded2 + rep.proj_err2, rel=2e-4,
+                                     abs=1e-6 * rep.normA2)
+    sg = out.s.double().cpu().numpy()
+    for t in ([0, p - 1] if p <= 10 else [0]):
+        Ah_t, U, s, V = _slice_oracle(A, Q, t)
+        assert np.linalg.norm(sg[t] - s[:k]) <= 1e-5 * np.linalg.norm(s[:k])
+        Ut = out.Uh[t].double().cpu().numpy()
+        Vt = out.Vh[t].double().cpu().numpy()
+        ref_k = (U[:, :k] * s[:k]) @ V[:, :k].T
+        gap = s[k - 1] / (s[k - 1] - s[k])
+        err = np.linalg.norm((Ut * sg[t]) @ Vt.T - ref_k) / np.linalg.norm(Ah_t)
+        assert err <= 1e-6 * (1 + 0.1 * gap), (err, gap)
+    # A_k lies in range(Q): A_k - (A_k x_3 Q^T) x_3 Q = 0
+    Ak = out.Ak
+    back = b.pprod_mode3(b.pprod_mode3(Ak, Qd, 0), Qd, 1)
+    assert float((Ak - back).norm()) <= 1e-5 * float(Ak.norm())
+
+
+@pytest.mark.parametrize("p,gamma", [(10, 0.99), (100, 0.9)])
+def test_hyperspectral_tsvdqII(data, p, gamma):
+    b = _b()
+    A, Qs = data
+    Q = Qs[p]
+    Ad, Qd = torch.from_numpy(A).cuda(), torch.from_numpy(Q).cuda()
+    out = b.tsvdqII(Ad, Qd, gamma)
+    full = b.tsvdq_trunc(Ad, Qd, 512, want_ak=False)
+    torch.cuda.synchronize()
+    rep = out.report()
+    assert rep.status == 0, b.status_str(rep.status)
+    sig = full.s.double().cpu().numpy()
+    K, rho, kept, total = oracle.select_energy(sig, gamma)          # bit-exact selection
+    assert rep.K == K and np.array_equal(out.rho.cpu().numpy(), rho)
+    assert rep.err2 == pytest.approx(rep.discarded2 + rep.proj_err2, rel=2e-4,
+                                     abs=1e-6 * rep.normA2)
+    assert rep.kept2 >= gamma * (rep.kept2 + rep.discarded2) * (1 - 1e-12)
+    _, _, s0, _ = _slice_oracle(A, Q, 0)
+    assert np.linalg.norm(sig[0] - s0) <= 1e-5 * np.linalg.norm(s0)
