@@ -334,6 +334,27 @@ def run_ours(args):
               "kappa": int(rpn.kappa), "speedup_p_lt_n": ms_pn / ms_per_step}
 
     # ---------------- end to end through host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world)
+
+    # ---------------- oracle CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.tsvdqII(A, Qp, GAMMA)
+        dt = time.perf_counter() - t0
+        cpu = {"value": L * M * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
+               "seconds": dt}
+    return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
+                  per_step_launches, clk, t_wall, dist)
+
+
+def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
+    """Same metric through host buffers: pinned A, Q copied in and the compressed
+    representation (report, rho, offs, packed factors) copied out every step."""
     A_h = torch.from_numpy(A).pin_memory()
     Q_h = torch.from_numpy(Qp).pin_memory()
     e2e_times = []
@@ -366,22 +387,14 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = {"value": world * L * M * N * args.steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(A.nbytes + Qp.nbytes),
-           "d2h_bytes_per_step": int(statistics.mean(d2h_bytes)),
-           "ms_per_step": 1e3 * e2e_s / args.steps}
+    return {"value": world * L * M * N * args.steps / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": int(A.nbytes + Qp.nbytes),
+            "d2h_bytes_per_step": int(statistics.mean(d2h_bytes)),
+            "ms_per_step": 1e3 * e2e_s / args.steps}
 
-    # ---------------- oracle CPU baseline (rank 0, N = 1 only)
-    cpu = None
-    if world == 1 and not args.no_cpu:
-        import oracle
-        t0 = time.perf_counter()
-        oracle.tsvdqII(A, Qp, GAMMA)
-        dt = time.perf_counter() - t0
-        cpu = {"value": L * M * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
-               "seconds": dt}
 
+def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
+           per_step_launches, clk, t_wall, dist):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -416,6 +429,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
