@@ -191,6 +191,32 @@ PP_API pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m,
                   size_t ws_bytes, void *stream);
 
 /*
+ * tsvdqII_noalloc: the same computation as tsvdqII for callers that cannot
+ * allocate device memory (no counterpart in the paper; it exists for callers
+ * whose device memory belongs to another allocator, latency-critical loops
+ * that forbid allocation after start-up because allocation can synchronise
+ * the device, and foreign-language bindings that only pass pointers they own).
+ * The caller passes inputs and outputs exactly as for tsvdqII but no
+ * workspace: the library uses one fixed device array of
+ * PP_NOALLOC_SCRATCH_BYTES bytes, held on every GPU that loads the library
+ * until the process exits.  Shapes whose tsvdqII workspace exceeds it return
+ * PP_EWORKSPACE before anything is enqueued (the video-shaped 120 x 160 x 300,
+ * p = 50 problem needs about 11.7 MB and fits).
+ * The first call on each device (with that device current) looks up the
+ * array's device address and may load the library's device module; make it
+ * before any stream capture.  Calls never allocate or free memory.  All calls
+ * on a device share the array and it keeps the last call's contents (each
+ * call resets what must start at zero): calls that may overlap on the GPU
+ * (unordered streams) race and must be serialised by the caller.
+ */
+#define PP_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+PP_API pp_status tsvdqII_noalloc(const float *A, const float *Q, int64_t l, int64_t m,
+                                 int64_t n, int64_t p, double gamma, int32_t *rho,
+                                 int64_t *offs, float *Uh_pk, float *s_pk, float *Vh_pk,
+                                 float *Ak, pp_report *rep, const pp_opts *opts,
+                                 void *stream);
+
+/*
  * Instrumentation for benchmarks (no counterpart in the paper).
  *
  * pp_set_stage_events: register up to 8 caller-created CUDA events

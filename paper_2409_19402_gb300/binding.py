@@ -75,6 +75,9 @@ def lib() -> ctypes.CDLL:
                               vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
         for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII"):
             getattr(L, f).restype = i32
+        L.tsvdqII_noalloc.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp,
+                                      vp, vp, vp, vp, ctypes.POINTER(pp_opts), vp]
+        L.tsvdqII_noalloc.restype = i32
         L.pp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         L.pp_set_stage_events.restype = None
         L.pp_kernel_launches.restype = ctypes.c_uint64
@@ -272,4 +275,27 @@ def tsvdqII(A: torch.Tensor, Q: torch.Tensor, gamma: float, want_ak: bool = True
     _raise(lib().tsvdqII(_ptr(A), _ptr(Q), l, m, n, p, float(gamma), _ptr(rho), _ptr(offs),
                          _ptr(Uh), _ptr(s), _ptr(Vh), _ptr(Ak), _ptr(rep), ctypes.byref(o),
                          _ptr(ws), 0 if ws is None else ws.numel(), _stream(stream)), "tsvdqII")
+    return TsvdqIIOut(rho, offs, Uh, s, Vh, Ak, rep, l, m)
+
+
+def tsvdqII_noalloc(A: torch.Tensor, Q: torch.Tensor, gamma: float, want_ak: bool = True,
+                    stream=None, **opts) -> TsvdqIIOut:
+    """Alg. 4.2 through tsvdqII_noalloc: no workspace argument, the library's
+    fixed device scratch array is used instead (outputs are still the caller's)."""
+    _check_t(A, "A"); _check_t(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    r = min(l, m)
+    dev = A.device
+    rho = torch.empty(p, dtype=torch.int32, device=dev)
+    offs = torch.empty(p + 1, dtype=torch.int64, device=dev)
+    Uh = torch.empty(p * r * l, dtype=torch.float32, device=dev)
+    s = torch.empty(p * r, dtype=torch.float32, device=dev)
+    Vh = torch.empty(p * r * m, dtype=torch.float32, device=dev)
+    Ak = torch.empty((n, l, m), dtype=torch.float32, device=dev) if want_ak else None
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    o = _opts(**opts)
+    _raise(lib().tsvdqII_noalloc(_ptr(A), _ptr(Q), l, m, n, p, float(gamma), _ptr(rho),
+                                 _ptr(offs), _ptr(Uh), _ptr(s), _ptr(Vh), _ptr(Ak), _ptr(rep),
+                                 ctypes.byref(o), _stream(stream)), "tsvdqII_noalloc")
     return TsvdqIIOut(rho, offs, Uh, s, Vh, Ak, rep, l, m)
