@@ -63,8 +63,8 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
   w.Ahk = c.take<float>(p * l * m);
   w.kept_p = c.take<double>(p);
   w.disc_p = c.take<double>(p);
-  w.part_a = c.take<double>(pp::sumsq_max_partials());
-  w.part_h = c.take<double>(pp::sumsq_max_partials());
+  w.part_a = c.take<double>(pp::mode3_gemm_max_partials(p, l * m));
+  w.part_h = c.take<double>(pp::mode3_gemm_max_partials(p, l * m));
   w.part_e = c.take<double>(pp::mode3_gemm_max_partials(n, l * m));
   w.scal = c.take<double>(8);
   w.status = c.take<int32_t>(1);
@@ -121,13 +121,13 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   PP_TRY(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
   if (o.check_q) PP_TRY(pp::launch_check_q(Q, n, p, o.q_tol, w.status, st));
   if (o.check_finite) PP_TRY(pp::launch_check_finite(A, n * l * m, w.status, st));
-  // Alg. 4.1 step 2: A-hat = A x_3 Q^T;  M(r, c) = Q^T(r, c) = Q[c*p + r]
-  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, nullptr, st));
-  int np = 0;
-  PP_TRY(pp::launch_sumsq(A, n * l * m, w.part_a, &np, st));
-  PP_TRY(pp::launch_sum_partials(w.part_a, np, w.scal + 0, st));
-  PP_TRY(pp::launch_sumsq(w.Ah, p * l * m, w.part_h, &np, st));
-  PP_TRY(pp::launch_sum_partials(w.part_h, np, w.scal + 1, st));
+  // Alg. 4.1 step 2: A-hat = A x_3 Q^T;  M(r, c) = Q^T(r, c) = Q[c*p + r], with the
+  // energies |A|^2 and |A-hat|^2 accumulated on the way
+  int np_h = 0, np_a = 0;
+  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_h, st,
+                               w.part_a, &np_a, w.part_h));
+  PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
+  PP_TRY(pp::launch_sum_partials(w.part_h, np_h, w.scal + 1, st));
   stage(1, st);
   // step 3: facewise SVD
   pp::JacobiArgs ja;

@@ -10,7 +10,9 @@
 //
 // Optionally the epilogue accumulates sum (Aref - Y)^2 in FP64 per CTA (the
 // reconstruction error |A - A_k|_F^2 of Thm. 4.2, fused into the
-// back-projection so A_k is never re-read).
+// back-projection so A_k is never re-read), and the projection accumulates the
+// energies |X|_F^2 (from the tiles it streams in) and |Y|_F^2 (from its
+// outputs) so that neither tensor is read a second time.
 #include "pp_internal.h"
 
 namespace pp {
@@ -37,8 +39,11 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
 __global__ void __launch_bounds__(NT) gemm_tile_kernel(
     const float *__restrict__ Qm, int64_t sr, int64_t sc, int64_t sMz,
     const float *__restrict__ X, int64_t sXz, float *__restrict__ Y, int64_t sYz, int64_t P,
-    // Y may be nullptr: only the error partials are produced
-    int64_t S, int64_t N, const float *__restrict__ Aref, double *__restrict__ errp) {
+    int64_t S, int64_t N, const float *__restrict__ Aref, double *__restrict__ errp,
+    double *__restrict__ xpart, double *__restrict__ ypart) {
+  // Y may be nullptr (only the error partials are produced); xpart / ypart may be
+  // nullptr.  xpart[blockIdx.x] (CTAs of the first row tile only) and
+  // ypart[CTA] receive the FP64 sums of squares of the X tiles and Y tile.
   __shared__ float Ms[BK][BM + 4];
   __shared__ __align__(16) float Xs[BK][BN];
   __shared__ double red[NT / 32];
@@ -56,6 +61,8 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
 
+  double xs = 0.0;
+  const bool do_x = xpart != nullptr && blockIdx.y == 0;
   for (int64_t c0 = 0; c0 < S; c0 += BK) {
     for (int e = tid; e < BM * BK; e += NT) {
       const int rr = e % BM, cc = e / BM;
@@ -65,7 +72,9 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(
     for (int e = tid; e < BK * BN; e += NT) {
       const int cc = e / BN, nn = e % BN;
       const int64_t c = c0 + cc, n = n0 + nn;
-      Xs[cc][nn] = (c < S && n < N) ? X[c * N + n] : 0.f;
+      const float v = (c < S && n < N) ? X[c * N + n] : 0.f;
+      Xs[cc][nn] = v;
+      if (do_x) xs += (double)v * v;
     }
     __syncthreads();
 #pragma unroll
@@ -84,7 +93,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(
     __syncthreads();
   }
 
-  double err = 0.0;
+  double err = 0.0, ys = 0.0;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int64_t r = r0 + ty * 4 + i;
@@ -94,16 +103,27 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(
       const int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
       if (n >= N) continue;
       if (Y) Y[r * N + n] = acc[i][j];
+      ys += (double)acc[i][j] * acc[i][j];
       if (Aref) {
         const double d = (double)Aref[z * sYz + r * N + n] - (double)acc[i][j];
         err += d * d;
       }
     }
   }
-  if (Aref) {  // uniform branch: every thread of the CTA takes it
+  const int64_t cta = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  if (Aref) {  // uniform branches: every thread of the CTA takes them
     const double s = block_sum_double(err, red);
-    if (tid == 0)
-      errp[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = s;
+    if (tid == 0) errp[cta] = s;
+    __syncthreads();
+  }
+  if (ypart) {
+    const double s = block_sum_double(ys, red);
+    if (tid == 0) ypart[cta] = s;
+    __syncthreads();
+  }
+  if (do_x) {
+    const double s = block_sum_double(xs, red);
+    if (tid == 0) xpart[blockIdx.x] = s;
   }
 }
 
@@ -115,12 +135,14 @@ int64_t mode3_gemm_max_partials(int64_t P, int64_t N) {
 
 cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const float *X,
                               float *Y, int64_t P, int64_t S, int64_t N, const float *Aref,
-                              double *err_partials, int *n_partials, cudaStream_t st) {
+                              double *err_partials, int *n_partials, cudaStream_t st,
+                              double *xpart, int *n_xpart, double *ypart) {
   const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((P + BM - 1) / BM), 1);
   if (n_partials) *n_partials = (int)(grid.x * grid.y);
+  if (n_xpart) *n_xpart = (int)grid.x;
   count_launch(1);
   gemm_tile_kernel<<<grid, NT, 0, st>>>(Qm, sr, sc, 0, X, 0, Y, 0, P, S, N, Aref,
-                                        err_partials);
+                                        err_partials, xpart, ypart);
   return cudaGetLastError();
 }
 
@@ -131,7 +153,7 @@ cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64
                   (unsigned)p);
   count_launch(1);
   gemm_tile_kernel<<<grid, NT, 0, st>>>(A, m, 1, n1 * m, B, m * n2, C, n1 * n2, n1, m, n2,
-                                        nullptr, nullptr);
+                                        nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -24,10 +24,14 @@ __device__ inline void set_status(int32_t *status, int32_t code) {
 // Y (P x N, row-major, ldY = N) = M (P x S) * X (S x N, row-major), with
 // M(r, c) = Qm[r * sr + c * sc].  When Aref != nullptr the launch also writes
 // sum (Aref - Y)^2 over each CTA tile to err_partials[CTA] (FP64); Y may then
-// be nullptr (error only).
+// be nullptr (error only).  Optional energy partials: xpart gets *n_xpart sums
+// of X^2 (each X entry counted once), ypart one sum of Y^2 per CTA
+// (*n_partials of them).
 cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const float *X,
                               float *Y, int64_t P, int64_t S, int64_t N, const float *Aref,
-                              double *err_partials, int *n_partials, cudaStream_t st);
+                              double *err_partials, int *n_partials, cudaStream_t st,
+                              double *xpart = nullptr, int *n_xpart = nullptr,
+                              double *ypart = nullptr);
 int64_t mode3_gemm_max_partials(int64_t P, int64_t N);
 
 // Batched facewise product C_t = A_t B_t (Def. 2.3).

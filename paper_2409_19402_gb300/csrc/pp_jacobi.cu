@@ -27,22 +27,31 @@
 // rotation angle is computed in FP32 with IEEE division and square roots;
 // FP64 is avoided in the inner loop because this part's FP64 rate is a small
 // fraction of its FP32 rate.
+#include <cooperative_groups.h>
+#include <stdio.h>
+#include <stdlib.h>
+
 #include "pp_internal.h"
 
 namespace pp {
 namespace {
 
+namespace cg = cooperative_groups;
+
 constexpr int NV_MAX = 6;                 // float4 chunks per lane per vector
 constexpr int SMEM_BUDGET = 200 * 1024;   // bytes of shared memory for vectors
 
 // Circle-method pairing of N (even) players: round r in [0, N-1), slot in [0, N/2).
+// Slot 0 pairs r with the fixed player N-1; slot s pairs r+s and r-s (mod N-1).
 __device__ __forceinline__ void circle_pair(int N, int r, int slot, int &j, int &k) {
   if (slot == 0) {
     j = r;
     k = N - 1;
   } else {
-    j = (r + slot) % (N - 1);
-    k = (r - slot + (N - 1)) % (N - 1);
+    j = r + slot;
+    if (j >= N - 1) j -= N - 1;
+    k = r - slot;
+    if (k < 0) k += N - 1;
   }
 }
 
@@ -144,6 +153,35 @@ __device__ __forceinline__ int block_or_count(int v, int *flag) {
   return s;
 }
 
+// Singular values of one slice from its converged vectors in global memory
+// (FP64-accumulated norms rounded to FP32) and the per-slice descending sort
+// (ties: lower vector index first).  nrm is b floats of shared scratch.
+__device__ void finish_slice(const float *Wg, int b, int a_pad, float *sig, int32_t *perm,
+                             float *nrm) {
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < b; j += nw) {
+    double acc = 0.0;
+    for (int e = lane; e < a_pad; e += 32) {
+      const float v = Wg[(int64_t)j * a_pad + e];
+      acc = fma((double)v, (double)v, acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) nrm[j] = (float)sqrt(acc);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < b; j += blockDim.x) {
+    const float sj = nrm[j];
+    int rank = 0;
+    for (int k = 0; k < b; ++k) {
+      const float sk = nrm[k];
+      rank += (sk > sj) || (sk == sj && k < j);
+    }
+    sig[rank] = sj;
+    perm[rank] = j;
+  }
+}
+
 constexpr int JAC_MAX_THREADS = 512;
 
 template <int G>
@@ -211,38 +249,279 @@ __global__ void __launch_bounds__(JAC_MAX_THREADS) jacobi_kernel(JacobiArgs A, i
   }
   __syncthreads();
 
-  // ---------------- singular values (FP64 accumulation) and the per-slice sort
-  float *sig_tmp = A.sig + f * b;          // unsorted norms first, then sorted in place below
-  int32_t *perm = A.perm + f * b;
-  // reuse shared memory: [0, b) floats hold the norms
-  float *nrm = Ws;
-  __syncthreads();
-  {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = warp; j < b; j += nw) {
-      double acc = 0.0;
-      for (int e = lane; e < a_pad; e += 32) {
-        const float v = Wg[(int64_t)j * a_pad + e];
-        acc = fma((double)v, (double)v, acc);
-      }
-      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-      if (lane == 0) nrm[j] = (float)sqrt(acc);
-    }
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < b; j += blockDim.x) {
-    const float sj = nrm[j];
-    int rank = 0;
-    for (int k = 0; k < b; ++k) {
-      const float sk = nrm[k];
-      rank += (sk > sj) || (sk == sj && k < j);
-    }
-    sig_tmp[rank] = sj;
-    perm[rank] = j;
-  }
+  finish_slice(Wg, b, a_pad, A.sig + f * b, A.perm + f * b, Ws);
   if (threadIdx.x == 0) {
     A.sweeps[f] = sweeps;
     if (!converged) set_status(A.status, PP_ENOCONV);
+  }
+}
+
+
+// ------------------------------------------------------------------ cluster kernel
+// One slice per thread-block cluster of C CTAs (C >= 2).  The b vectors are cut
+// into 2C blocks of bs vectors (vectors past b are zero and never rotate).
+// CTA c holds two blocks, on "seats" c and 2C-1-c of the round-robin circle
+// over blocks.  A sweep is 2C-1 block rounds: in each, a CTA orthogonalises
+// every cross pair of its two resident blocks (bs rounds of bs disjoint pairs
+// i <-> (i+r) mod bs); the first block round also covers the pairs inside each
+// block.  Between block rounds the blocks move one seat along the circle (seat
+// 0 fixed), which is a copy of at most two blocks into other CTAs' shared
+// memory (DSMEM) followed by one cluster barrier; shared memory is double
+// buffered so a CTA never overwrites blocks that are still being rotated.
+// After 2C-1 moves every block is back on its first seat.
+//
+// Few pairs are in flight per round here, so each pair gets a whole warp:
+// every lane holds at most CW float4 of each vector, and only the inner
+// product x.y is reduced across the warp.  The squared norms are tracked
+// (alpha' = alpha - t g, beta' = beta + t g for the rotation that zeroes g)
+// and recomputed from the vectors at the start of every block round, so the
+// tracking error never outlives bs + bs rotations; a sweep that rotates
+// nothing therefore tests orthogonality against freshly computed norms.
+
+// CW: float4 per lane per vector in the cluster kernel (a <= 128 * CW); 2, 4 or 6
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// One pair per group of GW lanes (16 or 32).  na, nb: tracked squared norms in
+// shared memory; lane is the lane index within the group.
+template <int GW, int CW>
+__device__ __forceinline__ bool jacobi_pair_warp(float *__restrict__ x, float *__restrict__ y,
+                                                 float *na, float *nb, int n4, float tol2,
+                                                 int lane, unsigned mask) {
+  float4 xv[CW], yv[CW];
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) {
+      xv[q] = reinterpret_cast<const float4 *>(x)[e4];
+      yv[q] = reinterpret_cast<const float4 *>(y)[e4];
+      g0 = fmaf(xv[q].x, yv[q].x, g0);
+      g1 = fmaf(xv[q].y, yv[q].y, g1);
+      g2 = fmaf(xv[q].z, yv[q].z, g2);
+      g3 = fmaf(xv[q].w, yv[q].w, g3);
+    }
+  }
+  float g = (g0 + g1) + (g2 + g3);
+#pragma unroll
+  for (int off = GW / 2; off > 0; off >>= 1) g += __shfl_xor_sync(mask, g, off, GW);
+  const float al = *na, be = *nb;
+  if (g == 0.f || g * g <= tol2 * al * be) return false;
+  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (be - al) / (2 g), written
+  // without zeta: t = sign(d) 2g / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
+  const float d = be - al, g2x = 2.f * g;
+  const float r = fmaf(d, d, g2x * g2x);
+  const float h = r * rsqrtf(r);
+  const float t = copysignf(1.f, d) * __fdividef(g2x, fabsf(d) + h);
+  const float u = fmaf(t, t, 1.f);
+  float c = rsqrtf(u);
+  c = c * fmaf(-0.5f * u * c, c, 1.5f);          // one Newton step: c = 1/sqrt(1 + t^2)
+  const float s = c * t;
+  // tau = s / (1 + c) (Rutishauser: implied cosine 1 - s tau), reciprocal refined
+  // by one Newton step so that tau is accurate to about half an ulp
+  const float onec = 1.f + c;                    // in [1, 2]: no special cases
+  float rc = __fdividef(1.f, onec);
+  rc = fmaf(rc, fmaf(-onec, rc, 1.f), rc);
+  const float tau = s * rc;
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) {
+      float4 nx, ny;
+      nx.x = fmaf(-s, fmaf(tau, xv[q].x, yv[q].x), xv[q].x);
+      ny.x = fmaf(s, fmaf(-tau, yv[q].x, xv[q].x), yv[q].x);
+      nx.y = fmaf(-s, fmaf(tau, xv[q].y, yv[q].y), xv[q].y);
+      ny.y = fmaf(s, fmaf(-tau, yv[q].y, xv[q].y), yv[q].y);
+      nx.z = fmaf(-s, fmaf(tau, xv[q].z, yv[q].z), xv[q].z);
+      ny.z = fmaf(s, fmaf(-tau, yv[q].z, xv[q].z), yv[q].z);
+      nx.w = fmaf(-s, fmaf(tau, xv[q].w, yv[q].w), xv[q].w);
+      ny.w = fmaf(s, fmaf(-tau, yv[q].w, xv[q].w), yv[q].w);
+      reinterpret_cast<float4 *>(x)[e4] = nx;
+      reinterpret_cast<float4 *>(y)[e4] = ny;
+    }
+  }
+  if (lane == 0) {
+    *na = fmaxf(fmaf(-t, g, al), 0.f);
+    *nb = fmaf(t, g, be);
+  }
+  return true;
+}
+
+// squared norms of `count` vectors (rows of a_pad floats), one warp per vector
+__device__ void block_norms(const float *v, float *nrm, int count, int n4) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < count; j += nw) {
+    float acc = 0.f;
+    for (int e4 = lane; e4 < n4; e4 += 32) {
+      const float4 w = reinterpret_cast<const float4 *>(v)[(size_t)j * n4 + e4];
+      acc = fmaf(w.x, w.x, fmaf(w.y, w.y, fmaf(w.z, w.z, fmaf(w.w, w.w, acc))));
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) nrm[j] = acc;
+  }
+}
+
+template <int GW>
+__device__ __forceinline__ unsigned group_mask() {
+  const int lane = threadIdx.x & 31;
+  return GW == 32 ? 0xffffffffu : (((1u << GW) - 1u) << (lane & ~(GW - 1)));
+}
+
+template <int GW, int CW>
+__device__ int cross_pass_warp(float *top, float *bot, float *ntop, float *nbot, int bs,
+                               int a_pad, float tol2) {
+  const int lane = threadIdx.x % GW, warp = threadIdx.x / GW, nw = blockDim.x / GW;
+  const unsigned mask = group_mask<GW>();
+  const int n4 = a_pad / 4;
+  int rot = 0;
+  for (int r = 0; r < bs; ++r) {
+    for (int i = warp; i < bs; i += nw) {
+      int j = i + r;
+      if (j >= bs) j -= bs;
+      if (jacobi_pair_warp<GW, CW>(top + (size_t)i * a_pad, bot + (size_t)j * a_pad, ntop + i,
+                                   nbot + j, n4, tol2, lane, mask) &&
+          lane == 0)
+        ++rot;
+    }
+    __syncthreads();
+  }
+  return rot;
+}
+
+template <int GW, int CW>
+__device__ int intra_pass_warp(float *top, float *bot, float *ntop, float *nbot, int bs,
+                               int a_pad, float tol2) {
+  const int lane = threadIdx.x % GW, warp = threadIdx.x / GW, nw = blockDim.x / GW;
+  const unsigned mask = group_mask<GW>();
+  const int n4 = a_pad / 4;
+  const int N = bs + (bs & 1), half = N / 2;
+  int rot = 0;
+  for (int r = 0; r < N - 1; ++r) {
+    for (int slot = warp; slot < 2 * half; slot += nw) {
+      const bool upper = slot < half;
+      float *base = upper ? top : bot;
+      float *nb = upper ? ntop : nbot;
+      int j, k;
+      circle_pair(N, r, upper ? slot : slot - half, j, k);
+      if (j >= bs || k >= bs) continue;
+      if (jacobi_pair_warp<GW, CW>(base + (size_t)j * a_pad, base + (size_t)k * a_pad, nb + j,
+                                   nb + k, n4, tol2, lane, mask) &&
+          lane == 0)
+        ++rot;
+    }
+    __syncthreads();
+  }
+  return rot;
+}
+
+// threads per CTA: GW lanes per pair, capped so that the registers fit
+__host__ __device__ constexpr int clu_max_threads(int gw, int cw) {
+  return (gw == 32 && cw <= 2) ? 1024 : 512;
+}
+
+template <int GW, int CW>
+__global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_kernel(JacobiArgs A, int a_pad,
+                                                                            int C, int bs) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ int blk[2][2];        // block id held in [buffer][top/bottom]
+  __shared__ int rot_total;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int64_t f = blockIdx.x / C;
+  const int l = (int)A.l, m = (int)A.m;
+  const bool rows = l <= m;
+  const int b = rows ? l : m, a = rows ? m : l;
+  const int n4 = a_pad / 4;
+  const int blk_floats = bs * a_pad;
+  const float tol2 = A.tol * A.tol;
+  const float *Xf = A.X + f * (int64_t)l * m;
+  float *Wg = A.W + f * (int64_t)b * a_pad;
+  auto slot = [&](int buf, int tb) { return sm + (size_t)(buf * 2 + tb) * blk_floats; };
+  float *ntop = sm + (size_t)4 * blk_floats;    // tracked squared norms of the resident blocks
+  float *nbot = ntop + bs;
+
+  // initial seats: top = block rank, bottom = block 2C-1-rank
+#pragma unroll
+  for (int tb = 0; tb < 2; ++tb) {
+    float *dst = slot(0, tb);
+    const int v0 = (tb == 0 ? rank : 2 * C - 1 - rank) * bs;
+    for (int idx = threadIdx.x; idx < blk_floats; idx += blockDim.x) {
+      const int j = v0 + idx / a_pad, e = idx % a_pad;
+      float v = 0.f;
+      if (j < b && e < a) v = rows ? Xf[(int64_t)j * m + e] : Xf[(int64_t)e * m + j];
+      dst[idx] = v;
+    }
+  }
+  if (threadIdx.x == 0) {
+    blk[0][0] = rank;
+    blk[0][1] = 2 * C - 1 - rank;
+    rot_total = 0;
+  }
+  cl.sync();
+
+  int cur = 0, sweeps = 0;
+  bool converged = false;
+  // destinations of this CTA's blocks when they move one seat
+  const int dst_top_rank = (rank == 0) ? 0 : (rank == C - 1 ? C - 1 : rank + 1);
+  const int dst_top_tb = (rank == C - 1) ? 1 : 0;
+  const int dst_bot_rank = (rank == 0) ? 1 : rank - 1;
+  const int dst_bot_tb = (rank == 0) ? 0 : 1;
+  while (sweeps < A.max_sweeps) {
+    ++sweeps;
+    int rot = 0;
+    for (int br = 0; br < 2 * C - 1; ++br) {
+      float *top = slot(cur, 0), *bot = slot(cur, 1);
+      block_norms(top, ntop, bs, n4);
+      block_norms(bot, nbot, bs, n4);
+      __syncthreads();
+      if (br == 0) rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+      rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+      // move the two blocks one seat along the circle (DSMEM copies)
+      const int nxt = cur ^ 1;
+#pragma unroll
+      for (int tb = 0; tb < 2; ++tb) {
+        const int dr = tb == 0 ? dst_top_rank : dst_bot_rank;
+        const int dtb = tb == 0 ? dst_top_tb : dst_bot_tb;
+        float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slot(nxt, dtb), dr));
+        const float4 *src = reinterpret_cast<const float4 *>(slot(cur, tb));
+        for (int idx = threadIdx.x; idx < blk_floats / 4; idx += blockDim.x) dst[idx] = src[idx];
+        if (threadIdx.x == 0) cl.map_shared_rank(&blk[0][0], dr)[nxt * 2 + dtb] = blk[cur][tb];
+      }
+      cl.sync();
+      cur = nxt;
+    }
+    if (rot) atomicAdd(cl.map_shared_rank(&rot_total, 0), rot);
+    cl.sync();
+    const int total = *cl.map_shared_rank(&rot_total, 0);
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0) rot_total = 0;   // next add is at least one barrier away
+    if (total == 0) {
+      converged = true;
+      break;
+    }
+  }
+  // write both resident blocks back to their places in W
+#pragma unroll
+  for (int tb = 0; tb < 2; ++tb) {
+    const int v0 = blk[cur][tb] * bs;
+    const float4 *src = reinterpret_cast<const float4 *>(slot(cur, tb));
+    for (int idx = threadIdx.x; idx < blk_floats / 4; idx += blockDim.x) {
+      const int j = v0 + idx / n4;
+      if (j < b) reinterpret_cast<float4 *>(Wg)[(int64_t)j * n4 + idx % n4] = src[idx];
+    }
+  }
+  __threadfence();
+  cl.sync();
+  if (rank == 0) {
+    finish_slice(Wg, b, a_pad, A.sig + f * b, A.perm + f * b, sm);
+    if (threadIdx.x == 0) {
+      A.sweeps[f] = sweeps;
+      if (!converged) set_status(A.status, PP_ENOCONV);
+    }
   }
 }
 
@@ -250,6 +529,124 @@ int pick_group(int64_t a) {
   if (a <= 192) return 8;
   if (a <= 384) return 16;
   return 32;
+}
+
+constexpr int NUM_SMS = 152;
+constexpr int MAX_CLUSTER = 8;
+
+size_t cluster_smem(int bs, int a_pad, int64_t b) {
+  size_t smem = (size_t)4 * bs * a_pad * sizeof(float) + (size_t)2 * bs * sizeof(float);
+  if ((int64_t)smem < b * 4) smem = (size_t)b * 4;
+  return smem;
+}
+
+// One cluster configuration: C CTAs per slice, GW lanes per pair, CW float4 per lane.
+struct ClusterCfg {
+  int C = 0, bs = 0, GW = 0, CW = 0, threads = 0;
+  size_t smem = 0;
+  int max_clusters = 0;   // co-resident clusters of this shape on the device
+};
+
+template <int GW, int CW>
+cudaError_t cluster_cfg_query(const JacobiArgs &A, int a_pad, int C, ClusterCfg &cc) {
+  const int64_t b = A.l < A.m ? A.l : A.m;
+  cc.C = C;
+  cc.bs = (int)((b + 2 * C - 1) / (2 * C));
+  cc.GW = GW;
+  cc.CW = CW;
+  int threads = GW * cc.bs;
+  if (threads > clu_max_threads(GW, CW)) threads = clu_max_threads(GW, CW);
+  cc.threads = (int)round_up(threads < 64 ? 64 : threads, 32);
+  cc.smem = cluster_smem(cc.bs, a_pad, b);
+  cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<GW, CW>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc.smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.p * C), 1, 1);
+  cfg.blockDim = dim3((unsigned)cc.threads, 1, 1);
+  cfg.dynamicSmemBytes = cc.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(&cc.max_clusters, jacobi_cluster_kernel<GW, CW>, &cfg);
+}
+
+template <int GW, int CW>
+cudaError_t cluster_launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc,
+                           cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(A.p * cc.C), 1, 1);
+  cfg.blockDim = dim3((unsigned)cc.threads, 1, 1);
+  cfg.dynamicSmemBytes = cc.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cc.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch(1);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<GW, CW>, A, a_pad, cc.C, cc.bs);
+}
+
+cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc) {
+  const int n4 = a_pad / 4;
+  if (GW == 16) {
+    if (n4 <= 48) return cluster_cfg_query<16, 3>(A, a_pad, C, cc);
+    if (n4 <= 64) return cluster_cfg_query<16, 4>(A, a_pad, C, cc);
+    return cluster_cfg_query<16, 8>(A, a_pad, C, cc);
+  }
+  if (n4 <= 64) return cluster_cfg_query<32, 2>(A, a_pad, C, cc);
+  if (n4 <= 128) return cluster_cfg_query<32, 4>(A, a_pad, C, cc);
+  return cluster_cfg_query<32, 6>(A, a_pad, C, cc);
+}
+
+cudaError_t launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStream_t st) {
+  if (cc.GW == 16) {
+    if (cc.CW == 3) return cluster_launch<16, 3>(A, a_pad, cc, st);
+    if (cc.CW == 4) return cluster_launch<16, 4>(A, a_pad, cc, st);
+    return cluster_launch<16, 8>(A, a_pad, cc, st);
+  }
+  if (cc.CW == 2) return cluster_launch<32, 2>(A, a_pad, cc, st);
+  if (cc.CW == 4) return cluster_launch<32, 4>(A, a_pad, cc, st);
+  return cluster_launch<32, 6>(A, a_pad, cc, st);
+}
+
+// Pick the cluster shape: among C in [2, 8] and GW in {16, 32} whose shared
+// memory fits, minimise (waves of co-resident clusters) / C, i.e. the
+// per-slice round time times the number of waves; ties prefer more CTAs per
+// slice, then the half-warp groups.  Returns false when no shape applies.
+bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
+  const int64_t b = A.l < A.m ? A.l : A.m;
+  double best_cost = 1e300;
+  bool found = false;
+  for (int C = MAX_CLUSTER; C >= 2; --C) {
+    if (b < 4 * C) continue;
+    const int bs = (int)((b + 2 * C - 1) / (2 * C));
+    if ((int64_t)cluster_smem(bs, a_pad, b) > SMEM_BUDGET) continue;
+    for (int GW : {16, 32}) {
+      ClusterCfg cc;
+      if (query(A, a_pad, C, GW, cc) != cudaSuccess || cc.max_clusters < 1) {
+        cudaGetLastError();
+        continue;
+      }
+      const double waves = (double)((A.p + cc.max_clusters - 1) / cc.max_clusters);
+      const double cost = waves / C;
+      if (cost < best_cost * (1.0 - 1e-9)) {
+        best_cost = cost;
+        best = cc;
+        found = true;
+      }
+    }
+  }
+  // a single CTA per slice already fills the machine when slices are many
+  if (found && best_cost >= 1.0 / 1.0 && A.p >= NUM_SMS / 2) found = false;
+  return found;
 }
 
 }  // namespace
@@ -267,6 +664,19 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
   const int G = pick_group(a);
   const int a_pad = (int)round_up(a, 4 * G);
   const int64_t row_bytes = (int64_t)a_pad * 4;
+  // cluster split when slices are few relative to the SMs
+  const bool log = getenv("PP_LOG_LAUNCH") != nullptr;   // shape of the chosen launch to stderr
+  if (A.p < NUM_SMS / 2) {
+    ClusterCfg cc;
+    if (pick_cluster(A, a_pad, cc)) {
+      if (log)
+        fprintf(stderr, "[pprod] jacobi cluster: p=%lld C=%d bs=%d GW=%d CW=%d threads=%d "
+                        "smem=%zu max_clusters=%d\n",
+                (long long)A.p, cc.C, cc.bs, cc.GW, cc.CW, cc.threads, cc.smem, cc.max_clusters);
+      return launch(A, a_pad, cc, st);
+    }
+  }
+  if (log) fprintf(stderr, "[pprod] jacobi single-CTA: p=%lld a_pad=%d\n", (long long)A.p, a_pad);
   int bs;                // block size in vectors; bs >= b means resident
   int64_t cap;           // vectors held in shared memory at once
   if (b * row_bytes <= SMEM_BUDGET) {

@@ -8,7 +8,8 @@
 // the slice ascending.  Each slice's values arrive sorted (descending), so
 // the global position of entry (t, j) is
 //   j + sum_{t' < t} #{sigma_{t'}^2 >= key} + sum_{t' > t} #{sigma_{t'}^2 > key},
-// computed with one binary search per other slice (a merge-path rank).  This
+// computed with one binary search per other slice (a merge-path rank), the
+// slices split over the lanes of one warp per entry.  This
 // is exact and deterministic, unlike a histogram-based radix select whose
 // FP64 bucket sums would depend on atomic ordering.  Keys are sigma^2 formed
 // in FP64 from the FP32 sigma (exact: a 24-bit significand squared fits).
@@ -23,23 +24,22 @@ namespace {
 
 constexpr int SEL_THREADS = 1024;
 
-__device__ __forceinline__ double key_of(const float *sig, int64_t idx) {
-  const double s = (double)sig[idx];
-  return s * s;
-}
-
-// number of entries of the descending row `row` (length b) with key' >= key (ge) or > key
-__device__ __forceinline__ int count_desc(const float *row, int b, double key, bool ge) {
+// Number of entries of the descending row `row` (length b) that come before a
+// value v from another slice: sigma' >= v (ge, the other slice has the lower
+// index) or sigma' > v.  sigma >= 0, so comparing the FP32 sigma is the same
+// as comparing the FP64 keys sigma^2 (exact squares, monotone).
+__device__ __forceinline__ int count_desc(const float *row, int b, float v, bool ge) {
   int lo = 0, hi = b;   // first index where the predicate fails
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    const double k2 = key_of(row, mid);
-    const bool in = ge ? (k2 >= key) : (k2 > key);
+    const float s2 = row[mid];
+    const bool in = ge ? (s2 >= v) : (s2 > v);
     if (in) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
+// One warp per entry (t, j): the lanes split the other slices' binary searches.
 __global__ void select_rank_kernel(const float *__restrict__ sig, int64_t p, int b,
                                    double *__restrict__ keys_sorted, int32_t *__restrict__ rank,
                                    int use_smem) {
@@ -51,18 +51,24 @@ __global__ void select_rank_kernel(const float *__restrict__ sig, int64_t p, int
     __syncthreads();
     src = ssig;
   }
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); e < N;
+       e += warps) {
     const int64_t t = e / b;
     const int j = (int)(e % b);
-    const double key = key_of(src, e);
-    int64_t pos = j;
-    for (int64_t t2 = 0; t2 < p; ++t2) {
+    const float v = src[e];
+    int64_t cnt = 0;
+    for (int64_t t2 = lane; t2 < p; t2 += 32) {
       if (t2 == t) continue;
-      pos += count_desc(src + t2 * b, b, key, t2 < t);
+      cnt += count_desc(src + t2 * b, b, v, t2 < t);
     }
-    rank[e] = (int32_t)pos;
-    keys_sorted[pos] = key;
+    for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, off);
+    if (lane == 0) {
+      const int64_t pos = j + cnt;
+      rank[e] = (int32_t)pos;
+      keys_sorted[pos] = (double)v * (double)v;
+    }
   }
 }
 
@@ -159,8 +165,8 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t st) {
   const int64_t N = a.p * a.b;
   const size_t smem_need = (size_t)N * sizeof(float);
   const int use_smem = smem_need <= 160 * 1024;
-  int blocks = (int)((N + 255) / 256);
-  if (blocks > 152 * 4) blocks = 152 * 4;
+  int blocks = (int)((N + 7) / 8);          // 8 warps (entries) per 256-thread block
+  if (blocks > 152 * 8) blocks = 152 * 8;
   cudaError_t e;
   if (use_smem) {
     e = cudaFuncSetAttribute(select_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -229,6 +229,12 @@ def test_tsvdqII_ragged_shapes(gamma):
     _tsvdqII_case(A, inputs.random_q(45, 7, seed=22), gamma)
 
 
+def test_tsvdqII_many_slices_single_cta_path():
+    """p >= 76 slices: one CTA per slice (no cluster split)."""
+    A = inputs.gaussian((100, 20, 30), seed=25)
+    _tsvdqII_case(A, inputs.random_q(100, 80, seed=26), 0.9)
+
+
 def test_tsvdqII_tall_slices():
     A = inputs.gaussian((20, 48, 30), seed=23)
     _tsvdqII_case(A, inputs.random_q(20, 6, seed=24), 0.95)
