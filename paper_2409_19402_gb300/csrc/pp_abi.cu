@@ -63,9 +63,9 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
   w.Ahk = c.take<float>(p * l * m);
   w.kept_p = c.take<double>(p);
   w.disc_p = c.take<double>(p);
-  w.part_a = c.take<double>(pp::mode3_gemm_max_partials(p, l * m));
-  w.part_h = c.take<double>(pp::mode3_gemm_max_partials(p, l * m));
-  w.part_e = c.take<double>(pp::mode3_gemm_max_partials(n, l * m));
+  w.part_a = c.take<double>(pp::mode3_tc_partials(p, l * m));
+  w.part_h = c.take<double>(pp::mode3_tc_partials(p, l * m));
+  w.part_e = c.take<double>(pp::mode3_tc_partials(n, l * m));
   w.scal = c.take<double>(8);
   w.status = c.take<int32_t>(1);
   w.K = c.take<int64_t>(1);
@@ -124,8 +124,8 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   // Alg. 4.1 step 2: A-hat = A x_3 Q^T;  M(r, c) = Q^T(r, c) = Q[c*p + r], with the
   // energies |A|^2 and |A-hat|^2 accumulated on the way
   int np_h = 0, np_a = 0;
-  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_h, st,
-                               w.part_a, &np_a, w.part_h));
+  PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_h, w.part_a,
+                             &np_a, w.part_h, w.status, st));
   PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
   PP_TRY(pp::launch_sum_partials(w.part_h, np_h, w.scal + 1, st));
   stage(1, st);
@@ -152,7 +152,8 @@ pp_status backproject(const float *A, const float *Q, int64_t l, int64_t m, int6
                       int64_t p, float *Ak, const DecompWs &w, cudaStream_t st) {
   int np = 0;
   // M(r, c) = Q(r, c) = Q[r*p + c]
-  PP_TRY(pp::launch_mode3_gemm(Q, p, 1, w.Ahk, Ak, n, p, l * m, A, w.part_e, &np, st));
+  PP_TRY(pp::launch_mode3_tc(Q, p, 1, w.Ahk, Ak, n, p, l * m, A, w.part_e, &np, nullptr, nullptr,
+                             nullptr, w.status, st));
   PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 2, st));
   return PP_OK;
 }
@@ -226,11 +227,11 @@ pp_status pprod_mode3(const float *X, int64_t l, int64_t m, int64_t n, const flo
   if (bad_dims(l, m, n, p)) return PP_ESHAPE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (transpose == 0)   // Y (p slices) = X (n slices) x_3 Q^T
-    return cuda_status(pp::launch_mode3_gemm(Q, 1, p, X, Y, p, n, l * m, nullptr, nullptr,
-                                             nullptr, st));
+    return cuda_status(pp::launch_mode3_tc(Q, 1, p, X, Y, p, n, l * m, nullptr, nullptr, nullptr,
+                                           nullptr, nullptr, nullptr, nullptr, st));
   // Y (n slices) = X (p slices) x_3 Q
-  return cuda_status(pp::launch_mode3_gemm(Q, p, 1, X, Y, n, p, l * m, nullptr, nullptr,
-                                           nullptr, st));
+  return cuda_status(pp::launch_mode3_tc(Q, p, 1, X, Y, n, p, l * m, nullptr, nullptr, nullptr,
+                                         nullptr, nullptr, nullptr, nullptr, st));
 }
 
 pp_status pprod_facewise(const float *Ah, const float *Bh, int64_t n1, int64_t m, int64_t n2,
@@ -256,10 +257,13 @@ pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1, int6
   float *Ah = c.take<float>(p * n1 * m);
   float *Bh = c.take<float>(p * m * n2);
   float *Ch = c.take<float>(p * n1 * n2);
-  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, A, Ah, p, n, n1 * m, nullptr, nullptr, nullptr, st));
-  PP_TRY(pp::launch_mode3_gemm(Q, 1, p, B, Bh, p, n, m * n2, nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, Ah, p, n, n1 * m, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_mode3_tc(Q, 1, p, B, Bh, p, n, m * n2, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, st));
   PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st));
-  PP_TRY(pp::launch_mode3_gemm(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_mode3_tc(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, st));
   return PP_OK;
 }
 

@@ -1,0 +1,348 @@
+// pp_gemm_tc.cu -- the mode-3 product (Def. 2.2) on the 5th-generation tensor
+// cores: Y (P x N) = M (P x S) * X (S x N) over the mode-3 unfolding, N = l*m
+// pixels.  This is the transform A x_3 Q^T of Alg. 4.1 step 2 and the reverse
+// transform x_3 Q of step 4.
+//
+// Tile: one CTA computes 128 pixels x NT = 64 output slices as
+// D[128 x NT] = X^T[128 x S] * M^T[S x NT] with tcgen05.mma kind::tf32, the
+// accumulator in tensor memory (TMEM).  FP32 accuracy is recovered with the
+// 3-pass split: every operand is written as hi = tf32(x) and lo = tf32(x - hi)
+// and the MMA accumulates hi*hi + hi*lo + lo*hi (the dropped lo*lo term and
+// the rounding of lo are below 2^-22 of each product).  The tensor core's own
+// accumulation is not round-to-nearest, and its error grows with the
+// magnitude of the accumulator; so each 32-wide chunk of S is accumulated
+// from zero in one of two TMEM buffers, and the chunk sums are added in FP32
+// registers (round to nearest) while the next chunk's MMAs run.
+//
+// Operands: the tensor is pixel-contiguous, i.e. MN-major for this product,
+// and M is tiny; both are streamed by the 128 threads of the CTA in chunks of
+// 32 along S and written into shared memory in the K-major, 128-byte-swizzled
+// canonical layout (row = pixel or slice, 32 tf32 = 128 bytes per row, 8-row
+// atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  Thread r owns
+// pixel row r: its 32 loads per chunk are coalesced across the warp.  Two
+// stages: while the MMAs of chunk c run, the threads fill chunk c+1; a stage
+// is refilled only after the tcgen05.commit of its previous MMAs has arrived
+// on that stage's mbarrier.  Every mbarrier wait is bounded; on expiry the
+// kernel records PP_ETIMEOUT, releases its TMEM and returns.
+//
+// Epilogue: each warp reads its 32 TMEM lanes (pixels) with tcgen05.ld and
+// stores the columns (slices) as coalesced 128-byte rows of Y, fusing the
+// optional sums |Aref - Y|^2, |Y|^2 and |X|^2 (FP64 per CTA).
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int TM = 128;        // pixels per CTA (MMA M)
+constexpr int TK = 32;         // S per stage: one 128-byte swizzle row of tf32
+constexpr int THREADS = 128;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// byte offset of element (row, k), k < 32, in a K-major SW128 tile
+__device__ __forceinline__ uint32_t sw128_chunk(int row, int chunk) {
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((chunk ^ row) & 7) << 4));
+}
+
+// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
+// atoms 1024 bytes apart (stride byte offset), version field 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // descriptor version
+  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M x N
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4)                      // D format f32
+         | (2u << 7)                    // A format tf32
+         | (2u << 10)                   // B format tf32
+         | ((uint32_t)(N >> 3) << 17)   // N / 8
+         | ((uint32_t)(M >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait: false after ~WAIT_CYCLES
+__device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(mbar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+  return true;
+}
+
+constexpr int NT = 64;   // output slices per CTA (MMA N)
+
+// thread tid adds the 64 columns of TMEM lane (32*warp + lane) of buffer `buf`
+// (chunk partial sums) into acc[]
+__device__ __forceinline__ void tmem_accumulate(uint32_t tmem, int buf, int warp, float *acc) {
+#pragma unroll
+  for (int j0 = 0; j0 < NT; j0 += 16) {
+    uint32_t r[16];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NT + j0);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[j0 + q] += __uint_as_float(r[q]);
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
+    const float *__restrict__ Qm, int64_t sr, int64_t sc, const float *__restrict__ X,
+    float *__restrict__ Y, int64_t P, int64_t S, int64_t N, const float *__restrict__ Aref,
+    double *__restrict__ errp, double *__restrict__ xpart, double *__restrict__ ypart,
+    int32_t *status) {
+  // stage layout (bytes): A_hi 16K | A_lo 16K | B_hi 8K | B_lo 8K
+  constexpr int A_BYTES = TM * 128, B_BYTES = NT * 128;
+  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int TMEM_COLS = 2 * NT;   // two chunk accumulators
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ double red[THREADS / 32];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * TM;
+  const int64_t y0 = (int64_t)blockIdx.y * NT;
+  const bool do_x = xpart != nullptr && blockIdx.y == 0;
+  constexpr uint32_t IDESC = tf32_idesc(TM, NT);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_sh)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_sh;
+
+  float acc[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) acc[j] = 0.f;
+  const int nchunks = (int)((S + TK - 1) / TK);
+  double xs = 0.0;
+  bool ok = true;
+  for (int c = 0; c < nchunks; ++c) {
+    const int st = c & 1;   // smem stage and TMEM buffer
+    unsigned char *base = smem + st * STAGE;
+    if (c >= 2) {   // chunk c-2 (same stage and buffer) must be complete: add its sums
+      if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)(((c - 2) >> 1) & 1))) ok = false;
+      if (__syncthreads_or(!ok)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      tmem_accumulate(tmem, st, warp, acc);
+    }
+    const int64_t s0 = (int64_t)c * TK;
+    // ---- A: pixel row tid, 32 values along S
+    {
+      float v[TK];
+      const int64_t pix = n0 + tid;
+#pragma unroll
+      for (int k = 0; k < TK; ++k) {
+        const int64_t s = s0 + k;
+        v[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
+      }
+      unsigned char *ah = base, *al = base + A_BYTES;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        float4 h, l;
+        h.x = tf32_rna(v[4 * ch + 0]); l.x = tf32_rna(v[4 * ch + 0] - h.x);
+        h.y = tf32_rna(v[4 * ch + 1]); l.y = tf32_rna(v[4 * ch + 1] - h.y);
+        h.z = tf32_rna(v[4 * ch + 2]); l.z = tf32_rna(v[4 * ch + 2] - h.z);
+        h.w = tf32_rna(v[4 * ch + 3]); l.w = tf32_rna(v[4 * ch + 3] - h.w);
+        const uint32_t off = sw128_chunk(tid, ch);
+        *reinterpret_cast<float4 *>(ah + off) = h;
+        *reinterpret_cast<float4 *>(al + off) = l;
+        if (do_x) {
+          xs += (double)v[4 * ch] * v[4 * ch] + (double)v[4 * ch + 1] * v[4 * ch + 1] +
+                (double)v[4 * ch + 2] * v[4 * ch + 2] + (double)v[4 * ch + 3] * v[4 * ch + 3];
+        }
+      }
+    }
+    // ---- B: output-slice row tid (< NT), 32 values along S: M(y0 + tid, s0 + k)
+    if (tid < NT) {
+      float v[TK];
+      const int64_t t = y0 + tid;
+#pragma unroll
+      for (int k = 0; k < TK; ++k) {
+        const int64_t s = s0 + k;
+        v[k] = (t < P && s < S) ? Qm[t * sr + s * sc] : 0.f;
+      }
+      unsigned char *bh = base + 2 * A_BYTES, *bl = bh + B_BYTES;
+#pragma unroll
+      for (int ch = 0; ch < 8; ++ch) {
+        float4 h, l;
+        h.x = tf32_rna(v[4 * ch + 0]); l.x = tf32_rna(v[4 * ch + 0] - h.x);
+        h.y = tf32_rna(v[4 * ch + 1]); l.y = tf32_rna(v[4 * ch + 1] - h.y);
+        h.z = tf32_rna(v[4 * ch + 2]); l.z = tf32_rna(v[4 * ch + 2] - h.z);
+        h.w = tf32_rna(v[4 * ch + 3]); l.w = tf32_rna(v[4 * ch + 3] - h.w);
+        const uint32_t off = sw128_chunk(tid, ch);
+        *reinterpret_cast<float4 *>(bh + off) = h;
+        *reinterpret_cast<float4 *>(bl + off) = l;
+      }
+    }
+    // generic-proxy writes -> visible to the tensor core (async proxy); the
+    // TMEM reads above are ordered before the MMAs that overwrite the buffer
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
+      const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+      const uint32_t d = tmem + (uint32_t)(st * NT);
+#pragma unroll
+      for (int kk = 0; kk < TK / 8; ++kk) {   // 8 tf32 = 32 bytes of K per MMA
+        const uint32_t o = 32u * kk;
+        mma_tf32(d, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, kk > 0 ? 1u : 0u);
+        mma_tf32(d, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, 1u);
+        mma_tf32(d, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, 1u);
+      }
+      mma_commit(smem_u32(&mbar[st]));
+    }
+  }
+  // the last two chunks
+  for (int c = (nchunks >= 2 ? nchunks - 2 : 0); ok && c < nchunks; ++c) {
+    const int st = c & 1;
+    if (!mbar_wait(smem_u32(&mbar[st]), (uint32_t)((c >> 1) & 1))) ok = false;
+    if (__syncthreads_or(!ok)) { ok = false; break; }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    tmem_accumulate(tmem, st, warp, acc);
+  }
+  ok = __syncthreads_and(ok);
+
+  double err = 0.0, ys = 0.0;
+  if (ok) {
+    const int64_t pix = n0 + warp * 32 + lane;
+    if (pix < N) {
+#pragma unroll
+      for (int q = 0; q < NT; ++q) {
+        const int64_t t = y0 + q;
+        if (t < P) {
+          const float v = acc[q];
+          if (Y) Y[t * N + pix] = v;
+          ys += (double)v * v;
+          if (Aref) {
+            const double d = (double)Aref[t * N + pix] - (double)v;
+            err += d * d;
+          }
+        }
+      }
+    }
+  } else if (tid == 0 && status) {
+    atomicCAS(status, 0, PP_ETIMEOUT);
+  }
+  // reductions (fixed order) of the fused sums
+  auto block_sum = [&](double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (tid == 0)
+      for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+    __syncthreads();
+    return s;
+  };
+  const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  if (Aref) {
+    const double s = block_sum(err);
+    if (tid == 0) errp[cta] = s;
+  }
+  if (ypart) {
+    const double s = block_sum(ys);
+    if (tid == 0) ypart[cta] = s;
+  }
+  if (do_x) {
+    const double s = block_sum(xs);
+    if (tid == 0) xpart[blockIdx.x] = s;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS));
+  }
+}
+
+size_t tc_smem() {
+  return (size_t)2 * (2 * TM * 128 + 2 * NT * 128) + 1024;   // 2 stages + alignment slack
+}
+
+}  // namespace
+
+int64_t mode3_tc_partials(int64_t P, int64_t N) {
+  return ((N + TM - 1) / TM) * ((P + NT - 1) / NT);
+}
+
+cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
+                            int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
+                            int *n_partials, double *xpart, int *n_xpart, double *ypart,
+                            int32_t *status, cudaStream_t st) {
+  if (n_partials) *n_partials = (int)(((N + TM - 1) / TM) * ((P + NT - 1) / NT));
+  if (n_xpart) *n_xpart = (int)((N + TM - 1) / TM);
+  const size_t smem = tc_smem();
+  cudaError_t e = cudaFuncSetAttribute(mode3_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), 1);
+  count_launch(1);
+  mode3_tc_kernel<<<grid, THREADS, smem, st>>>(Qm, sr, sc, X, Y, P, S, N, Aref, errp, xpart,
+                                               ypart, status);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

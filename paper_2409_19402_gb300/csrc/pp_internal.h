@@ -34,6 +34,15 @@ cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const flo
                               double *ypart = nullptr);
 int64_t mode3_gemm_max_partials(int64_t P, int64_t N);
 
+// Tensor-core (tcgen05, 3-pass split TF32) version of launch_mode3_gemm with
+// the same operands and fused sums; partial counts from mode3_tc_partials.
+// A bounded wait that expires writes PP_ETIMEOUT to *status (if non-null).
+cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
+                            int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
+                            int *n_partials, double *xpart, int *n_xpart, double *ypart,
+                            int32_t *status, cudaStream_t st);
+int64_t mode3_tc_partials(int64_t P, int64_t N);
+
 // Batched facewise product C_t = A_t B_t (Def. 2.3).
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
                                  int64_t m, int64_t n2, int64_t p, cudaStream_t st);

@@ -274,11 +274,12 @@ __global__ void __launch_bounds__(JAC_MAX_THREADS) jacobi_kernel(JacobiArgs A, i
 // every lane holds at most CW float4 of each vector, and only the inner
 // product x.y is reduced across the warp.  The squared norms are tracked
 // (alpha' = alpha - t g, beta' = beta + t g for the rotation that zeroes g)
-// and recomputed from the vectors at the start of every block round, so the
-// tracking error never outlives bs + bs rotations; a sweep that rotates
-// nothing therefore tests orthogonality against freshly computed norms.
+// travel with their blocks; they are recomputed from the vectors at the start
+// of every sweep, so a sweep that rotates nothing tests orthogonality against
+// freshly computed norms.
 
 // CW: float4 per lane per vector in the cluster kernel (a <= 128 * CW); 2, 4 or 6
+constexpr int CLU_MAX_BS = 64;   // largest block (vectors) the cluster kernel takes
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -441,8 +442,9 @@ __global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_ker
   const float *Xf = A.X + f * (int64_t)l * m;
   float *Wg = A.W + f * (int64_t)b * a_pad;
   auto slot = [&](int buf, int tb) { return sm + (size_t)(buf * 2 + tb) * blk_floats; };
-  float *ntop = sm + (size_t)4 * blk_floats;    // tracked squared norms of the resident blocks
-  float *nbot = ntop + bs;
+  // tracked squared norms, double buffered like the blocks: [buf][top/bottom][bs]
+  float *nrm_base = sm + (size_t)4 * blk_floats;
+  auto nslot = [&](int buf, int tb) { return nrm_base + (size_t)(buf * 2 + tb) * bs; };
 
   // initial seats: top = block rank, bottom = block 2C-1-rank
 #pragma unroll
@@ -475,10 +477,13 @@ __global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_ker
     int rot = 0;
     for (int br = 0; br < 2 * C - 1; ++br) {
       float *top = slot(cur, 0), *bot = slot(cur, 1);
-      block_norms(top, ntop, bs, n4);
-      block_norms(bot, nbot, bs, n4);
-      __syncthreads();
-      if (br == 0) rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+      float *ntop = nslot(cur, 0), *nbot = nslot(cur, 1);
+      if (br == 0) {   // fresh norms once per sweep; afterwards they travel with the blocks
+        block_norms(top, ntop, bs, n4);
+        block_norms(bot, nbot, bs, n4);
+        __syncthreads();
+        rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+      }
       rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
       // move the two blocks one seat along the circle (DSMEM copies)
       const int nxt = cur ^ 1;
@@ -489,6 +494,9 @@ __global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_ker
         float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slot(nxt, dtb), dr));
         const float4 *src = reinterpret_cast<const float4 *>(slot(cur, tb));
         for (int idx = threadIdx.x; idx < blk_floats / 4; idx += blockDim.x) dst[idx] = src[idx];
+        float *dn = cl.map_shared_rank(nslot(nxt, dtb), dr);
+        const float *sn = nslot(cur, tb);
+        for (int i = threadIdx.x; i < bs; i += blockDim.x) dn[i] = sn[i];
         if (threadIdx.x == 0) cl.map_shared_rank(&blk[0][0], dr)[nxt * 2 + dtb] = blk[cur][tb];
       }
       cl.sync();
@@ -535,8 +543,8 @@ constexpr int NUM_SMS = 152;
 constexpr int MAX_CLUSTER = 8;
 
 size_t cluster_smem(int bs, int a_pad, int64_t b) {
-  size_t smem = (size_t)4 * bs * a_pad * sizeof(float) + (size_t)2 * bs * sizeof(float);
-  if ((int64_t)smem < b * 4) smem = (size_t)b * 4;
+  size_t smem = (size_t)4 * bs * a_pad * sizeof(float) + (size_t)4 * bs * sizeof(float);
+  if ((int64_t)smem < b * 4) smem = (size_t)b * 4;   // finish_slice: b norms
   return smem;
 }
 
@@ -628,6 +636,7 @@ bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
   for (int C = MAX_CLUSTER; C >= 2; --C) {
     if (b < 4 * C) continue;
     const int bs = (int)((b + 2 * C - 1) / (2 * C));
+    if (bs > CLU_MAX_BS) continue;
     if ((int64_t)cluster_smem(bs, a_pad, b) > SMEM_BUDGET) continue;
     for (int GW : {16, 32}) {
       ClusterCfg cc;
