@@ -18,16 +18,18 @@
 // and M is tiny; both are streamed by the 128 threads of the CTA in chunks of
 // 32 along S and written into shared memory in the K-major, 128-byte-swizzled
 // canonical layout (row = pixel or slice, 32 tf32 = 128 bytes per row, 8-row
-// atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  Thread r owns
-// pixel row r: its 32 loads per chunk are coalesced across the warp.  Two
+// atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  Each load of a
+// warp covers 32 consecutive pixels (coalesced).  Two
 // stages: while the MMAs of chunk c run, the threads fill chunk c+1; a stage
 // is refilled only after the tcgen05.commit of its previous MMAs has arrived
 // on that stage's mbarrier.  Every mbarrier wait is bounded; on expiry the
 // kernel records PP_ETIMEOUT, releases its TMEM and returns.
 //
-// Epilogue: each warp reads its 32 TMEM lanes (pixels) with tcgen05.ld and
-// stores the columns (slices) as coalesced 128-byte rows of Y, fusing the
-// optional sums |Aref - Y|^2, |Y|^2 and |X|^2 (FP64 per CTA).
+// 256 threads: threads r and r + 128 share pixel row r (each converts half of
+// the chunk's 32 values) and, in the epilogue, half of the 64 output columns
+// of TMEM lane r (tcgen05.ld), which they store as coalesced 128-byte rows of
+// Y, fusing the optional sums |Aref - Y|^2, |Y|^2 and |X|^2 (FP32 over a few
+// terms, FP64 beyond).
 #include "pp_internal.h"
 
 namespace pp {
@@ -35,7 +37,7 @@ namespace {
 
 constexpr int TM = 128;        // pixels per CTA (MMA M)
 constexpr int TK = 32;         // S per stage: one 128-byte swizzle row of tf32
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;   // two threads per pixel row (halves of K and of the columns)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -112,13 +114,14 @@ __device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
 
 constexpr int NT = 64;   // output slices per CTA (MMA N)
 
-// thread tid adds the 64 columns of TMEM lane (32*warp + lane) of buffer `buf`
-// (chunk partial sums) into acc[]
+// warp w adds columns [32 (w / 4), 32 (w / 4) + 32) of TMEM lanes 32 (w % 4) ... + 31 of
+// buffer `buf` (chunk partial sums) into acc[] (one TMEM lane per thread)
 __device__ __forceinline__ void tmem_accumulate(uint32_t tmem, int buf, int warp, float *acc) {
 #pragma unroll
-  for (int j0 = 0; j0 < NT; j0 += 16) {
+  for (int j0 = 0; j0 < NT / 2; j0 += 16) {
     uint32_t r[16];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * NT + j0);
+    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) +
+                           (uint32_t)(buf * NT + (warp >> 2) * (NT / 2) + j0);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -170,9 +173,11 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_sh;
 
-  float acc[NT];
+  float acc[NT / 2];
 #pragma unroll
-  for (int j = 0; j < NT; ++j) acc[j] = 0.f;
+  for (int j = 0; j < NT / 2; ++j) acc[j] = 0.f;
+  const int row = tid & (TM - 1);          // pixel row / slice row owned by this thread
+  const int khalf = tid >> 7;              // which 16 of the 32 K values (0 or 1)
   const int nchunks = (int)((S + TK - 1) / TK);
   double xs = 0.0;
   bool ok = true;
@@ -186,50 +191,52 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
       tmem_accumulate(tmem, st, warp, acc);
     }
     const int64_t s0 = (int64_t)c * TK;
-    // ---- A: pixel row tid, 32 values along S
+    // ---- A: pixel row `row`, 16 values along S (this thread's half of the chunk)
     {
-      float v[TK];
-      const int64_t pix = n0 + tid;
+      float v[TK / 2];
+      const int64_t pix = n0 + row;
 #pragma unroll
-      for (int k = 0; k < TK; ++k) {
-        const int64_t s = s0 + k;
+      for (int k = 0; k < TK / 2; ++k) {
+        const int64_t s = s0 + khalf * (TK / 2) + k;
         v[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
       }
       unsigned char *ah = base, *al = base + A_BYTES;
+      float xq = 0.f;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const int ch = khalf * 4 + c4;
         float4 h, l;
-        h.x = tf32_rna(v[4 * ch + 0]); l.x = tf32_rna(v[4 * ch + 0] - h.x);
-        h.y = tf32_rna(v[4 * ch + 1]); l.y = tf32_rna(v[4 * ch + 1] - h.y);
-        h.z = tf32_rna(v[4 * ch + 2]); l.z = tf32_rna(v[4 * ch + 2] - h.z);
-        h.w = tf32_rna(v[4 * ch + 3]); l.w = tf32_rna(v[4 * ch + 3] - h.w);
-        const uint32_t off = sw128_chunk(tid, ch);
+        h.x = tf32_rna(v[4 * c4 + 0]); l.x = tf32_rna(v[4 * c4 + 0] - h.x);
+        h.y = tf32_rna(v[4 * c4 + 1]); l.y = tf32_rna(v[4 * c4 + 1] - h.y);
+        h.z = tf32_rna(v[4 * c4 + 2]); l.z = tf32_rna(v[4 * c4 + 2] - h.z);
+        h.w = tf32_rna(v[4 * c4 + 3]); l.w = tf32_rna(v[4 * c4 + 3] - h.w);
+        const uint32_t off = sw128_chunk(row, ch);
         *reinterpret_cast<float4 *>(ah + off) = h;
         *reinterpret_cast<float4 *>(al + off) = l;
-        if (do_x) {
-          xs += (double)v[4 * ch] * v[4 * ch] + (double)v[4 * ch + 1] * v[4 * ch + 1] +
-                (double)v[4 * ch + 2] * v[4 * ch + 2] + (double)v[4 * ch + 3] * v[4 * ch + 3];
-        }
+        xq = fmaf(v[4 * c4], v[4 * c4], fmaf(v[4 * c4 + 1], v[4 * c4 + 1],
+             fmaf(v[4 * c4 + 2], v[4 * c4 + 2], fmaf(v[4 * c4 + 3], v[4 * c4 + 3], xq))));
       }
+      if (do_x) xs += (double)xq;   // FP32 over 16 values, FP64 across chunks
     }
-    // ---- B: output-slice row tid (< NT), 32 values along S: M(y0 + tid, s0 + k)
-    if (tid < NT) {
-      float v[TK];
-      const int64_t t = y0 + tid;
+    // ---- B: output-slice row `row` (< NT), 16 values along S: M(y0 + row, s0 + k)
+    if (row < NT) {
+      float v[TK / 2];
+      const int64_t t = y0 + row;
 #pragma unroll
-      for (int k = 0; k < TK; ++k) {
-        const int64_t s = s0 + k;
+      for (int k = 0; k < TK / 2; ++k) {
+        const int64_t s = s0 + khalf * (TK / 2) + k;
         v[k] = (t < P && s < S) ? Qm[t * sr + s * sc] : 0.f;
       }
       unsigned char *bh = base + 2 * A_BYTES, *bl = bh + B_BYTES;
 #pragma unroll
-      for (int ch = 0; ch < 8; ++ch) {
+      for (int c4 = 0; c4 < 4; ++c4) {
+        const int ch = khalf * 4 + c4;
         float4 h, l;
-        h.x = tf32_rna(v[4 * ch + 0]); l.x = tf32_rna(v[4 * ch + 0] - h.x);
-        h.y = tf32_rna(v[4 * ch + 1]); l.y = tf32_rna(v[4 * ch + 1] - h.y);
-        h.z = tf32_rna(v[4 * ch + 2]); l.z = tf32_rna(v[4 * ch + 2] - h.z);
-        h.w = tf32_rna(v[4 * ch + 3]); l.w = tf32_rna(v[4 * ch + 3] - h.w);
-        const uint32_t off = sw128_chunk(tid, ch);
+        h.x = tf32_rna(v[4 * c4 + 0]); l.x = tf32_rna(v[4 * c4 + 0] - h.x);
+        h.y = tf32_rna(v[4 * c4 + 1]); l.y = tf32_rna(v[4 * c4 + 1] - h.y);
+        h.z = tf32_rna(v[4 * c4 + 2]); l.z = tf32_rna(v[4 * c4 + 2] - h.z);
+        h.w = tf32_rna(v[4 * c4 + 3]); l.w = tf32_rna(v[4 * c4 + 3] - h.w);
+        const uint32_t off = sw128_chunk(row, ch);
         *reinterpret_cast<float4 *>(bh + off) = h;
         *reinterpret_cast<float4 *>(bl + off) = l;
       }
@@ -266,20 +273,27 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
 
   double err = 0.0, ys = 0.0;
   if (ok) {
-    const int64_t pix = n0 + warp * 32 + lane;
+    const int64_t pix = n0 + (warp & 3) * 32 + lane;       // TMEM lane of this thread
+    const int64_t c0 = y0 + (warp >> 2) * (NT / 2);        // first of its 32 columns
     if (pix < N) {
 #pragma unroll
-      for (int q = 0; q < NT; ++q) {
-        const int64_t t = y0 + q;
-        if (t < P) {
-          const float v = acc[q];
-          if (Y) Y[t * N + pix] = v;
-          ys += (double)v * v;
-          if (Aref) {
-            const double d = (double)Aref[t * N + pix] - (double)v;
-            err += d * d;
+      for (int g = 0; g < NT / 2; g += 8) {     // FP32 over 8 values, FP64 across groups
+        float e8 = 0.f, y8 = 0.f;
+#pragma unroll
+        for (int q = g; q < g + 8; ++q) {
+          const int64_t t = c0 + q;
+          if (t < P) {
+            const float v = acc[q];
+            if (Y) Y[t * N + pix] = v;
+            y8 = fmaf(v, v, y8);
+            if (Aref) {
+              const float d = Aref[t * N + pix] - v;
+              e8 = fmaf(d, d, e8);
+            }
           }
         }
+        ys += (double)y8;
+        err += (double)e8;
       }
     }
   } else if (tid == 0 && status) {

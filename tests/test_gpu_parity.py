@@ -162,7 +162,8 @@ def test_tsvdq_trunc(case):
     sig_all = np.stack([oracle.svd(x)[1] for x in oracle.mode3(A, f64(Q).T)])
     _check_recon(host(out.Ak), rep.err2, Ak, ref.err2, A, sig_all, [k] * Q.shape[1])
     assert rep.discarded2 == pytest.approx(ref.discarded2, rel=1e-5, abs=1e-6 * ref.normA2)
-    assert rep.normA2 == pytest.approx(ref.normA2, rel=1e-12)
+    # energies: FP32 partial sums over <= 16 terms, combined in FP64 (<= 16 u relative)
+    assert rep.normA2 == pytest.approx(ref.normA2, rel=16 * U32)
     assert rep.kappa == k * Q.shape[1] and rep.K == 0
     # factors: orthonormal columns and sigma_q u_q v_q^T matches per slice
     U, V = host(out.Uh), host(out.Vh)
