@@ -75,7 +75,8 @@ typedef enum pp_op {
     PP_OP_FACEWISE = 1,
     PP_OP_PPROD = 2,
     PP_OP_TSVDQ = 3,
-    PP_OP_TSVDQII = 4
+    PP_OP_TSVDQII = 4,
+    PP_OP_HOSVD = 5
 } pp_op;
 
 /* Problem sizes for pp_workspace_bytes.  Fields an op does not use are
@@ -111,6 +112,17 @@ typedef struct pp_report {
     double proj_err2;     /* |A|^2 - |A x_3 Q^T|^2: projection error of Thm 4.2,    */
                           /* exact only for orthonormal Q; suffers cancellation    */
 } pp_report;
+
+/* Device-written report of hosvd_compare. */
+typedef struct pp_hosvd_report {
+    int32_t status;       /* PP_OK or a device-detected pp_status                  */
+    int32_t sweeps;       /* largest Jacobi sweep count over the p slices          */
+    int64_t k1, k2, k;    /* HOSVD ranks (k1, k2, p) and the *Q-SVD rank min(k1,k2) */
+    double normA2;        /* |A|_F^2                                               */
+    double err2_hosvd;    /* |A - A_(k1,k2,p)|_F^2, truncated HOSVD with U3 = Q     */
+    double err2_tsvdq;    /* |A - A_k|_F^2, truncated *Q-SVD with k = min(k1, k2)  */
+    double proj_err2;     /* |A|^2 - |A x_3 Q^T|^2 (common projection error)       */
+} pp_hosvd_report;
 
 /* Human-readable name of a status code (static string). */
 PP_API const char *pp_status_str(int32_t status);
@@ -191,6 +203,23 @@ PP_API pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m,
                   int64_t *offs, float *Uh_pk, float *s_pk, float *Vh_pk,
                   float *Ak, pp_report *rep, const pp_opts *opts, void *ws,
                   size_t ws_bytes, void *stream);
+
+/*
+ * Truncated HOSVD against the *Q-SVD (Sec. 4.2, Thm. 4.6).
+ *   A is l x m x n, Q is n x p (the mode-3 factor U3), 1 <= k1 <= l, 1 <= k2 <= m.
+ * U1, U2 are the leading k1 / k2 eigenvectors of the Gram matrices of the
+ * mode-1 / mode-2 unfoldings (eq. modek_svd); the HOSVD approximation is
+ * A_(k1,k2,p) = A x_1 U1U1^T x_2 U2U2^T x_3 QQ^T.  The *Q-SVD (Alg. 4.1) is run
+ * with k = min(k1, k2) on the same Q; Thm. 4.6 states err2_tsvdq <= err2_hosvd
+ * when Q = U3(:, 1:p).  Ak_hosvd (n x l x m) may be NULL; rep (device) receives
+ * both squared errors.  Workspace: pp_workspace_bytes(PP_OP_HOSVD, {l, m, n, p,
+ * k = k1, n2 = k2}).
+ */
+PP_API pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m,
+                               int64_t n, int64_t p, int64_t k1, int64_t k2,
+                               float *Ak_hosvd, pp_hosvd_report *rep,
+                               const pp_opts *opts, void *ws, size_t ws_bytes,
+                               void *stream);
 
 /*
  * tsvdqII_noalloc: the same computation as tsvdqII for callers that cannot

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpprod.so")
 
 PP_OK, PP_EINVAL, PP_ESHAPE, PP_ENOTORTHO, PP_ENONFINITE, PP_ENOCONV = 0, 1, 2, 3, 4, 5
 PP_ETIMEOUT, PP_EWORKSPACE, PP_ECUDA, PP_ENOSYS = 6, 7, 8, 9
-PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII = 0, 1, 2, 3, 4
+PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII, PP_OP_HOSVD = 0, 1, 2, 3, 4, 5
 
 
 class PPError(RuntimeError):
@@ -49,7 +49,15 @@ class pp_report(ctypes.Structure):
                 ("proj_err2", ctypes.c_double)]
 
 
+class pp_hosvd_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("k1", ctypes.c_int64),
+                ("k2", ctypes.c_int64), ("k", ctypes.c_int64), ("normA2", ctypes.c_double),
+                ("err2_hosvd", ctypes.c_double), ("err2_tsvdq", ctypes.c_double),
+                ("proj_err2", ctypes.c_double)]
+
+
 REPORT_BYTES = ctypes.sizeof(pp_report)
+HOSVD_REPORT_BYTES = ctypes.sizeof(pp_hosvd_report)
 _lib = None
 
 
@@ -75,6 +83,9 @@ def lib() -> ctypes.CDLL:
                               vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
         for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII"):
             getattr(L, f).restype = i32
+        L.hosvd_compare.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, vp, vp,
+                                    ctypes.POINTER(pp_opts), vp, sz, vp]
+        L.hosvd_compare.restype = i32
         L.tsvdqII_noalloc.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp,
                                       vp, vp, vp, vp, ctypes.POINTER(pp_opts), vp]
         L.tsvdqII_noalloc.restype = i32
@@ -299,3 +310,24 @@ def tsvdqII_noalloc(A: torch.Tensor, Q: torch.Tensor, gamma: float, want_ak: boo
                                  _ptr(offs), _ptr(Uh), _ptr(s), _ptr(Vh), _ptr(Ak), _ptr(rep),
                                  ctypes.byref(o), _stream(stream)), "tsvdqII_noalloc")
     return TsvdqIIOut(rho, offs, Uh, s, Vh, Ak, rep, l, m)
+
+
+def hosvd_compare(A: torch.Tensor, Q: torch.Tensor, k1: int, k2: int, want_ak: bool = False,
+                  ws=None, stream=None, **opts):
+    """Sec. 4.2: truncated HOSVD (k1, k2, p) with U3 = Q against the *Q-SVD with
+    k = min(k1, k2).  Returns (pp_hosvd_report, A_hosvd or None); synchronises."""
+    _check_t(A, "A"); _check_t(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    dev = A.device
+    Ak = torch.empty((n, l, m), dtype=torch.float32, device=dev) if want_ak else None
+    rep = torch.zeros(HOSVD_REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_HOSVD, l=l, m=m, n=n, p=p, k=k1, n2=k2)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().hosvd_compare(_ptr(A), _ptr(Q), l, m, n, p, int(k1), int(k2), _ptr(Ak),
+                               _ptr(rep), ctypes.byref(o), _ptr(ws),
+                               0 if ws is None else ws.numel(), _stream(stream)), "hosvd_compare")
+    raw = bytes(rep.cpu().numpy().tobytes())
+    return pp_hosvd_report.from_buffer_copy(raw), Ak

@@ -76,6 +76,44 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
   return w;
 }
 
+struct HosvdWs {
+  DecompWs d;
+  float *Uk, *sk, *Vk;                       // *Q-SVD factors at k = min(k1, k2)
+  float *gpart, *G1, *G2;                    // Gram partials and the two Grams
+  float *Wg, *sigg;                          // Jacobi of a Gram matrix (one slice)
+  int32_t *permg, *sweepsg;
+  float *U1, *s1, *V1, *U2, *s2, *V2;        // leading eigenvectors (V1, V2 are used)
+  float *P1, *P2, *T;                        // projectors and the slice-wise temporary
+};
+
+HosvdWs carve_hosvd(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, int64_t k1,
+                    int64_t k2) {
+  HosvdWs h;
+  h.d = carve_decomp(c, l, m, n, p, false);
+  const int64_t k = k1 < k2 ? k1 : k2;
+  const int64_t d = l > m ? l : m;
+  h.Uk = c.take<float>(p * l * k);
+  h.sk = c.take<float>(p * k);
+  h.Vk = c.take<float>(p * m * k);
+  h.gpart = c.take<float>(pp::gram_groups(n) * d * d);
+  h.G1 = c.take<float>(l * l);
+  h.G2 = c.take<float>(m * m);
+  h.Wg = c.take<float>(d * pp::jacobi_apad(d, d));
+  h.sigg = c.take<float>(d);
+  h.permg = c.take<int32_t>(d);
+  h.sweepsg = c.take<int32_t>(1);
+  h.U1 = c.take<float>(l * k1);
+  h.s1 = c.take<float>(k1);
+  h.V1 = c.take<float>(l * k1);
+  h.U2 = c.take<float>(m * k2);
+  h.s2 = c.take<float>(k2);
+  h.V2 = c.take<float>(m * k2);
+  h.P1 = c.take<float>(l * l);
+  h.P2 = c.take<float>(m * m);
+  h.T = c.take<float>(p * l * m);
+  return h;
+}
+
 pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUDA; }
 
 #define PP_TRY(expr)                            \
@@ -214,6 +252,12 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
     case PP_OP_TSVDQII:
       if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
       carve_decomp(c, sh->l, sh->m, sh->n, sh->p, op == PP_OP_TSVDQII);
+      return c.off;
+    case PP_OP_HOSVD:
+      if (bad_dims(sh->l, sh->m, sh->n, sh->p) || sh->k < 1 || sh->k > sh->l || sh->n2 < 1 ||
+          sh->n2 > sh->m)
+        return 0;
+      carve_hosvd(c, sh->l, sh->m, sh->n, sh->p, sh->k, sh->n2);
       return c.off;
     default:
       return 0;
@@ -400,6 +444,112 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
     PP_TRY(pp::launch_report(ra, st));
   }
   stage(5, st);
+  return PP_OK;
+}
+
+pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                        int64_t p, int64_t k1, int64_t k2, float *Ak_hosvd, pp_hosvd_report *rep,
+                        const pp_opts *opts, void *ws, size_t ws_bytes, void *stream) {
+  if (!A || !Q) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  if (k1 < 1 || k1 > l || k2 < 1 || k2 > m) return PP_ESHAPE;
+  if ((l > m ? l : m) > MAX_LONG_SIDE) return PP_ENOSYS;
+  pp_shape sh{l, m, n, p, k1, k2};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_HOSVD, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const HosvdWs h = carve_hosvd(c, l, m, n, p, k1, k2);
+  const DecompWs &w = h.d;
+  const int64_t b = l < m ? l : m;
+  const int64_t k = k1 < k2 ? k1 : k2;
+  // (1) *Q-SVD with k = min(k1, k2) (Alg. 4.1), its error in scal[2]
+  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  pp::FactorArgs fa;
+  fa.X = w.Ah;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = l;
+  fa.m = m;
+  fa.p = p;
+  fa.b = b;
+  fa.a_pad = pp::jacobi_apad(l, m);
+  fa.kfix = k;
+  fa.rho = nullptr;
+  fa.offs = nullptr;
+  fa.Uh = h.Uk;
+  fa.s = h.sk;
+  fa.Vh = h.Vk;
+  fa.Ahk = w.Ahk;
+  fa.kept_partial = w.kept_p;
+  fa.disc_partial = w.disc_p;
+  PP_TRY(pp::launch_factors(fa, st));
+  if (pp_status e = backproject(A, Q, l, m, n, p, nullptr, w, st)) return e;
+  // (2) HOSVD factors: leading eigenvectors of the mode-1 and mode-2 Grams (eq. modek_svd)
+  for (int mode = 1; mode <= 2; ++mode) {
+    const int64_t d = mode == 1 ? l : m, kd = mode == 1 ? k1 : k2;
+    float *G = mode == 1 ? h.G1 : h.G2;
+    PP_TRY(pp::launch_gram(A, l, m, n, mode, h.gpart, G, st));
+    pp::JacobiArgs ja;
+    ja.X = G;
+    ja.W = h.Wg;
+    ja.sig = h.sigg;
+    ja.perm = h.permg;
+    ja.sweeps = h.sweepsg;
+    ja.status = w.status;
+    ja.l = d;
+    ja.m = d;
+    ja.p = 1;
+    ja.max_sweeps = o.max_sweeps;
+    ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(d, d);
+    PP_TRY(pp::launch_jacobi(ja, st));
+    pp::FactorArgs fg;
+    fg.X = G;
+    fg.W = h.Wg;
+    fg.sig = h.sigg;
+    fg.perm = h.permg;
+    fg.l = d;
+    fg.m = d;
+    fg.p = 1;
+    fg.b = d;
+    fg.a_pad = pp::jacobi_apad(d, d);
+    fg.kfix = kd;
+    fg.rho = nullptr;
+    fg.offs = nullptr;
+    fg.Uh = mode == 1 ? h.U1 : h.U2;
+    fg.s = mode == 1 ? h.s1 : h.s2;
+    fg.Vh = mode == 1 ? h.V1 : h.V2;
+    fg.Ahk = nullptr;
+    fg.kept_partial = nullptr;
+    fg.disc_partial = nullptr;
+    PP_TRY(pp::launch_factors(fg, st));
+    PP_TRY(pp::launch_projector(mode == 1 ? h.V1 : h.V2, d, kd, mode == 1 ? h.P1 : h.P2, st));
+  }
+  // (3) slice-wise P1 A-hat_t P2, then x_3 Q with the fused error in scal[3]
+  PP_TRY(pp::launch_batched_gemm(w.Ah, m, 1, l * m, h.P2, 0, h.T, l * m, l, m, m, p, st));
+  PP_TRY(pp::launch_batched_gemm(h.P1, l, 1, 0, h.T, l * m, w.Ahk, l * m, l, l, m, p, st));
+  {
+    int np = 0;
+    PP_TRY(pp::launch_mode3_tc(Q, p, 1, w.Ahk, Ak_hosvd, n, p, l * m, A, w.part_e, &np, nullptr,
+                               nullptr, nullptr, w.status, st));
+    PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 3, st));
+  }
+  if (rep) {
+    pp::HosvdReportArgs ra;
+    ra.rep = rep;
+    ra.status = w.status;
+    ra.sweeps = w.sweeps;
+    ra.p = p;
+    ra.k1 = k1;
+    ra.k2 = k2;
+    ra.k = k;
+    ra.normA2 = w.scal + 0;
+    ra.normAh2 = w.scal + 1;
+    ra.err2_tsvdq = w.scal + 2;
+    ra.err2_hosvd = w.scal + 3;
+    PP_TRY(pp::launch_hosvd_report(ra, st));
+  }
   return PP_OK;
 }
 

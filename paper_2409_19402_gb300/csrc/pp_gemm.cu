@@ -146,6 +146,16 @@ cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const flo
   return cudaGetLastError();
 }
 
+cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                                const float *X, int64_t sXz, float *Y, int64_t sYz, int64_t P,
+                                int64_t S, int64_t N, int64_t batch, cudaStream_t st) {
+  const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((P + BM - 1) / BM), (unsigned)batch);
+  count_launch(1);
+  gemm_tile_kernel<<<grid, NT, 0, st>>>(Mm, sr, sc, sMz, X, sXz, Y, sYz, P, S, N, nullptr,
+                                        nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
                                  int64_t m, int64_t n2, int64_t p, cudaStream_t st) {
   // slice t: C_t (n1 x n2) = A_t (n1 x m) * B_t (m x n2); A_t(r, c) = A[t*n1*m + r*m + c]

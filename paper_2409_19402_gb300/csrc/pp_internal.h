@@ -43,6 +43,13 @@ cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float
                             int32_t *status, cudaStream_t st);
 int64_t mode3_tc_partials(int64_t P, int64_t N);
 
+// Batched FP32 GEMM Y[z] (P x N) = M[z] (P x S) * X[z] (S x N), M(r, c) =
+// Mm[z*sMz + r*sr + c*sc], X and Y row-major with leading dimension N; a batch
+// stride of 0 broadcasts an operand over the batch.
+cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                                const float *X, int64_t sXz, float *Y, int64_t sYz, int64_t P,
+                                int64_t S, int64_t N, int64_t batch, cudaStream_t st);
+
 // Batched facewise product C_t = A_t B_t (Def. 2.3).
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
                                  int64_t m, int64_t n2, int64_t p, cudaStream_t st);
@@ -104,6 +111,24 @@ cudaError_t launch_sum_partials(const double *partials, int n_partials, double *
 cudaError_t launch_check_q(const float *Q, int64_t n, int64_t p, float tol, int32_t *status,
                            cudaStream_t st);
 cudaError_t launch_check_finite(const float *x, int64_t n, int32_t *status, cudaStream_t st);
+
+// ---------------------------------------------------------------- HOSVD (Sec. 4.2)
+int64_t gram_groups(int64_t n);
+// G (d x d) = Gram of the mode-`mode` unfolding (1: d = l, 2: d = m) of A (n slices
+// l x m); part holds gram_groups(n) partial d x d matrices.
+cudaError_t launch_gram(const float *A, int64_t l, int64_t m, int64_t n, int mode, float *part,
+                        float *G, cudaStream_t st);
+// P (d x d) = U U^T for U d x k row-major.
+cudaError_t launch_projector(const float *U, int64_t d, int64_t k, float *P, cudaStream_t st);
+
+struct HosvdReportArgs {
+  pp_hosvd_report *rep;
+  const int32_t *status;
+  const int32_t *sweeps;
+  int64_t p, k1, k2, k;
+  const double *normA2, *normAh2, *err2_tsvdq, *err2_hosvd;
+};
+cudaError_t launch_hosvd_report(const HosvdReportArgs &a, cudaStream_t st);
 
 struct ReportArgs {
   pp_report *rep;

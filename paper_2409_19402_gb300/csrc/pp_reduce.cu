@@ -96,9 +96,32 @@ __global__ void report_kernel(ReportArgs a) {
   *a.rep = r;
 }
 
+__global__ void hosvd_report_kernel(HosvdReportArgs a) {
+  if (threadIdx.x != 0) return;
+  pp_hosvd_report r;
+  r.status = *a.status;
+  int32_t sw = 0;
+  for (int64_t t = 0; t < a.p; ++t) sw = max(sw, a.sweeps[t]);
+  r.sweeps = sw;
+  r.k1 = a.k1;
+  r.k2 = a.k2;
+  r.k = a.k;
+  r.normA2 = *a.normA2;
+  r.err2_hosvd = *a.err2_hosvd;
+  r.err2_tsvdq = *a.err2_tsvdq;
+  r.proj_err2 = r.normA2 - *a.normAh2;
+  *a.rep = r;
+}
+
 }  // namespace
 
 int64_t sumsq_max_partials() { return RED_BLOCKS; }
+
+cudaError_t launch_hosvd_report(const HosvdReportArgs &a, cudaStream_t st) {
+  count_launch(1);
+  hosvd_report_kernel<<<1, 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sumsq(const float *x, int64_t n, double *partials, int *n_partials,
                          cudaStream_t st) {
