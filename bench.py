@@ -91,7 +91,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -262,6 +262,10 @@ def run_ours(args):
     Qp_d = torch.from_numpy(Qp).to(dev)
     Qn_d = torch.from_numpy(Qn).to(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # launch-shape autotuning of the Jacobi SVD on this problem (setup, untimed)
+    from paper_2409_19402_gb300 import autotune
+    tuned = autotune.tune_jacobi(A_d, Qp_d, gamma=GAMMA, use_cache=False)
+    tuned_n = autotune.tune_jacobi(A_d, Qn_d, gamma=GAMMA, use_cache=False) if not args.no_pn else None
     run = Runner(A_d, Qp_d, GAMMA, torch, binding)
 
     # stage events: created by recording once, then registered with the library
@@ -273,12 +277,11 @@ def run_ours(args):
 
     # ---------------- timed region (p < n)
     launches0 = binding.kernel_launches()
-    clocks = ClockSampler(local)       # samples warm-up + timed steps (200 ms period)
+    clocks = ClockSampler(local)       # samples warm-up + timed steps (20 ms period)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    time.sleep(0.25)                   # let the sampler take its first reading under load
     t_wall0 = time.perf_counter()
     times, stage_ms = timed_steps(run, args.steps, args.warmup, torch, flush, stream,
                                   stage_events)
@@ -346,6 +349,7 @@ def run_ours(args):
         rpn = run_pn.report()
         ms_pn = sum(t_pn) / args.steps
         pn = {"p": N, "gamma": gamma_pn, "ms_per_step": ms_pn,
+              "jacobi_shape": {"C": tuned_n[0], "GW": tuned_n[1]},
               "value": L * M * N / (ms_pn / 1e3), "err2": rpn.err2, "err2_target": err_target,
               "kappa": int(rpn.kappa), "speedup_p_lt_n": ms_pn / ms_per_step}
 
@@ -365,7 +369,7 @@ def run_ours(args):
                "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
                "seconds": dt}
     return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-                  per_step_launches, clk, t_wall, dist)
+                  per_step_launches, clk, t_wall, dist, tuned)
 
 
 def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
@@ -410,7 +414,7 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-           per_step_launches, clk, t_wall, dist):
+           per_step_launches, clk, t_wall, dist, tuned=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -421,6 +425,7 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "flushed before every step (256 MiB write), outside the events",
                        "K": int(rep.K), "kappa": int(rep.kappa), "sweeps": int(rep.sweeps),
+                       "jacobi_shape": {"C": tuned[0], "GW": tuned[1]},
                        "RE": math.sqrt(rep.err2 / rep.normA2)},
             "roofline": roofline,
             "stages": stages,

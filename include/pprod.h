@@ -264,6 +264,18 @@ PP_API pp_status tsvdqII_noalloc(const float *A, const float *Q, int64_t l, int6
 PP_API void pp_set_stage_events(void *const *events, int32_t n);
 PP_API uint64_t pp_kernel_launches(void);
 
+/*
+ * Launch-shape tuning of the facewise Jacobi SVD (no counterpart in the paper).
+ * For slices of l x m, p of them per call, use C CTAs per slice (C = 1: one
+ * CTA per slice; 2..8: a thread-block cluster of C CTAs exchanging vector
+ * blocks through distributed shared memory) and GW lanes per rotated pair (8,
+ * 16 or 32).  A registered shape overrides the built-in choice when it can be
+ * launched; C = 0 removes the entry.  Process-wide; returns PP_EINVAL for
+ * unsupported values.  The Python autotuner (autotune.py) times the candidates
+ * and registers the fastest.
+ */
+PP_API pp_status pp_set_jacobi_shape(int64_t l, int64_t m, int64_t p, int32_t C, int32_t GW);
+
 #ifdef __cplusplus
 }
 #endif

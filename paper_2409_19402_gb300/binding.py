@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
         L.tsvdqII_noalloc.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp,
                                       vp, vp, vp, vp, ctypes.POINTER(pp_opts), vp]
         L.tsvdqII_noalloc.restype = i32
+        L.pp_set_jacobi_shape.argtypes = [i64, i64, i64, i32, i32]
+        L.pp_set_jacobi_shape.restype = i32
         L.pp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         L.pp_set_stage_events.restype = None
         L.pp_kernel_launches.restype = ctypes.c_uint64
@@ -117,6 +119,11 @@ def set_stage_events(events) -> None:
         return
     arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
     lib().pp_set_stage_events(arr, len(events))
+
+
+def set_jacobi_shape(l: int, m: int, p: int, C: int, GW: int = 16) -> None:
+    """Register the Jacobi launch shape for l x m slices, p per call (C = 0 removes it)."""
+    _raise(lib().pp_set_jacobi_shape(int(l), int(m), int(p), int(C), int(GW)), "pp_set_jacobi_shape")
 
 
 def workspace_bytes(op: int, l=0, m=0, n=0, p=0, k=0, n2=0) -> int:

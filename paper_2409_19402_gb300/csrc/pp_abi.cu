@@ -235,6 +235,10 @@ void pp_set_stage_events(void *const *events, int32_t n) {
 
 uint64_t pp_kernel_launches(void) { return pp::g_launches.load(); }
 
+pp_status pp_set_jacobi_shape(int64_t l, int64_t m, int64_t p, int32_t C, int32_t GW) {
+  return pp::set_jacobi_shape(l, m, p, C, GW) ? PP_OK : PP_EINVAL;
+}
+
 size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
   if (!sh) return 0;
   Carve c(nullptr);

@@ -67,6 +67,8 @@ struct JacobiArgs {
   float tol;          // rotation threshold on |cos|
 };
 int64_t jacobi_apad(int64_t l, int64_t m);
+// register (C >= 1) or remove (C = 0) the Jacobi launch shape for l x m slices, p of them
+bool set_jacobi_shape(int64_t l, int64_t m, int64_t p, int C, int GW);
 cudaError_t launch_jacobi(const JacobiArgs &a, cudaStream_t st);
 
 // ---------------------------------------------------------------- select (Alg. 4.2)

@@ -31,6 +31,10 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "pp_internal.h"
 
 namespace pp {
@@ -421,7 +425,7 @@ __device__ int intra_pass_warp(float *top, float *bot, float *ntop, float *nbot,
 
 // threads per CTA: GW lanes per pair, capped so that the registers fit
 __host__ __device__ constexpr int clu_max_threads(int gw, int cw) {
-  return (gw == 32 && cw <= 2) ? 1024 : 512;
+  return (gw * cw <= 64 && gw >= 32) ? 1024 : 512;
 }
 
 template <int GW, int CW>
@@ -542,6 +546,10 @@ int pick_group(int64_t a) {
 constexpr int NUM_SMS = 152;
 constexpr int MAX_CLUSTER = 8;
 
+// registered launch shapes (pp_set_jacobi_shape): (l, m, p) -> (C, GW)
+std::mutex g_shape_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t>, std::pair<int, int>> g_shapes;
+
 size_t cluster_smem(int bs, int a_pad, int64_t b) {
   size_t smem = (size_t)4 * bs * a_pad * sizeof(float) + (size_t)4 * bs * sizeof(float);
   if ((int64_t)smem < b * 4) smem = (size_t)b * 4;   // finish_slice: b norms
@@ -604,6 +612,10 @@ cudaError_t cluster_launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc,
 
 cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc) {
   const int n4 = a_pad / 4;
+  if (GW == 8) {
+    if (n4 <= 40) return cluster_cfg_query<8, 5>(A, a_pad, C, cc);
+    return cluster_cfg_query<8, 8>(A, a_pad, C, cc);
+  }
   if (GW == 16) {
     if (n4 <= 48) return cluster_cfg_query<16, 3>(A, a_pad, C, cc);
     if (n4 <= 64) return cluster_cfg_query<16, 4>(A, a_pad, C, cc);
@@ -615,6 +627,10 @@ cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc)
 }
 
 cudaError_t launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStream_t st) {
+  if (cc.GW == 8) {
+    if (cc.CW == 5) return cluster_launch<8, 5>(A, a_pad, cc, st);
+    return cluster_launch<8, 8>(A, a_pad, cc, st);
+  }
   if (cc.GW == 16) {
     if (cc.CW == 3) return cluster_launch<16, 3>(A, a_pad, cc, st);
     if (cc.CW == 4) return cluster_launch<16, 4>(A, a_pad, cc, st);
@@ -625,27 +641,36 @@ cudaError_t launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStr
   return cluster_launch<32, 6>(A, a_pad, cc, st);
 }
 
-// Pick the cluster shape: among C in [2, 8] and GW in {16, 32} whose shared
-// memory fits, minimise (waves of co-resident clusters) / C, i.e. the
-// per-slice round time times the number of waves; ties prefer more CTAs per
-// slice, then the half-warp groups.  Returns false when no shape applies.
+// Pick the cluster shape: among C in [2, 8] and GW in {8, 16, 32} whose shared
+// memory fits, minimise waves x (rounds + barrier cost) per sweep, where a sweep
+// has 2 C bs - 1 pair rounds (bs = ceil(b / 2C): padding vectors cost rounds)
+// and 2C + 1 cluster barriers (each counted as two rounds), and the round time
+// grows with the group's reduction depth log2(GW).  Returns false when no
+// shape applies.
 bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
   const int64_t b = A.l < A.m ? A.l : A.m;
   double best_cost = 1e300;
   bool found = false;
+  // tuning overrides (environment): PP_JACOBI_C in [2, 8], PP_JACOBI_GW in {16, 32}
+  const char *envC = getenv("PP_JACOBI_C"), *envG = getenv("PP_JACOBI_GW");
+  const int forceC = envC ? atoi(envC) : 0, forceG = envG ? atoi(envG) : 0;
   for (int C = MAX_CLUSTER; C >= 2; --C) {
+    if (forceC && C != forceC) continue;
     if (b < 4 * C) continue;
     const int bs = (int)((b + 2 * C - 1) / (2 * C));
     if (bs > CLU_MAX_BS) continue;
     if ((int64_t)cluster_smem(bs, a_pad, b) > SMEM_BUDGET) continue;
-    for (int GW : {16, 32}) {
+    for (int GW : {8, 16, 32}) {
+      if (forceG && GW != forceG) continue;
+      if (GW == 8 && a_pad / 4 > 64) continue;
       ClusterCfg cc;
       if (query(A, a_pad, C, GW, cc) != cudaSuccess || cc.max_clusters < 1) {
         cudaGetLastError();
         continue;
       }
       const double waves = (double)((A.p + cc.max_clusters - 1) / cc.max_clusters);
-      const double cost = waves / C;
+      const double depth = GW == 8 ? 3.0 : (GW == 16 ? 4.0 : 5.0);
+      const double cost = waves * (2.0 * C * bs - 1.0 + 2.0 * (2 * C + 1)) * (1.0 + 0.15 * depth);
       if (cost < best_cost * (1.0 - 1e-9)) {
         best_cost = cost;
         best = cc;
@@ -653,12 +678,20 @@ bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
       }
     }
   }
-  // a single CTA per slice already fills the machine when slices are many
-  if (found && best_cost >= 1.0 / 1.0 && A.p >= NUM_SMS / 2) found = false;
   return found;
 }
 
 }  // namespace
+
+bool set_jacobi_shape(int64_t l, int64_t m, int64_t p, int C, int GW) {
+  if (l < 1 || m < 1 || p < 1 || C < 0 || C > MAX_CLUSTER) return false;
+  if (C >= 2 && GW != 8 && GW != 16 && GW != 32) return false;
+  std::lock_guard<std::mutex> lock(g_shape_mu);
+  const auto key = std::make_tuple(l, m, p);
+  if (C == 0) g_shapes.erase(key);
+  else g_shapes[key] = std::make_pair(C, GW);
+  return true;
+}
 
 int64_t jacobi_apad(int64_t l, int64_t m) {
   const int64_t a = l > m ? l : m;
@@ -675,7 +708,26 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
   const int64_t row_bytes = (int64_t)a_pad * 4;
   // cluster split when slices are few relative to the SMs
   const bool log = getenv("PP_LOG_LAUNCH") != nullptr;   // shape of the chosen launch to stderr
-  if (A.p < NUM_SMS / 2) {
+  int regC = -1, regG = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_shape_mu);
+    auto it = g_shapes.find(std::make_tuple(A.l, A.m, A.p));
+    if (it != g_shapes.end()) { regC = it->second.first; regG = it->second.second; }
+  }
+  if (regC >= 2) {   // a registered cluster shape, if it can be launched
+    ClusterCfg cc;
+    const int bs = (int)((b + 2 * regC - 1) / (2 * regC));
+    if (b >= 4 * regC && bs <= CLU_MAX_BS &&
+        (int64_t)cluster_smem(bs, a_pad, b) <= SMEM_BUDGET &&
+        query(A, a_pad, regC, regG, cc) == cudaSuccess && cc.max_clusters >= 1) {
+      if (log)
+        fprintf(stderr, "[pprod] jacobi cluster (registered): p=%lld C=%d bs=%d GW=%d\n",
+                (long long)A.p, cc.C, cc.bs, cc.GW);
+      return launch(A, a_pad, cc, st);
+    }
+    cudaGetLastError();
+  }
+  if (regC < 0 && A.p < NUM_SMS / 2) {
     ClusterCfg cc;
     if (pick_cluster(A, a_pad, cc)) {
       if (log)

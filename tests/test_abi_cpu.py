@@ -101,3 +101,21 @@ def test_binding_refuses_cpu_tensors():
     b = _lib()
     with pytest.raises(ValueError):
         b.pprod_mode3(torch.zeros(4, 2, 2), torch.zeros(4, 2), 0)
+
+
+def test_jacobi_shape_registration_validates_on_host():
+    b = _lib()
+    L = b.lib()
+    assert L.pp_set_jacobi_shape(120, 160, 50, 9, 16) == b.PP_EINVAL     # C > 8
+    assert L.pp_set_jacobi_shape(120, 160, 50, 3, 12) == b.PP_EINVAL     # GW not 8/16/32
+    assert L.pp_set_jacobi_shape(0, 160, 50, 3, 16) == b.PP_EINVAL
+    assert L.pp_set_jacobi_shape(120, 160, 50, 5, 16) == b.PP_OK
+    assert L.pp_set_jacobi_shape(120, 160, 50, 0, 0) == b.PP_OK          # removal
+
+
+def test_autotune_candidates():
+    from paper_2409_19402_gb300 import autotune
+    c = autotune.candidates(120, 160)
+    assert (1, 16) in c and (5, 16) in c and (8, 32) in c
+    assert all(C == 1 or 120 >= 4 * C for C, _ in c)
+    assert autotune.candidates(6, 9) == [(1, 16)]
