@@ -222,6 +222,35 @@ PP_API pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_
                                void *stream);
 
 /*
+ * Batched *Q-SVDII over independent tensors of uneven sizes (one item per
+ * tensor: its own A, Q, sizes, outputs, report and workspace slice, exactly as
+ * the arguments of tsvdqII).  Items are spread over a small set of auxiliary
+ * streams that fork from `stream` and join back into it (events), so the
+ * tensors' kernels overlap on the GPU; the call enqueues everything and
+ * returns, with no allocation and no synchronisation, so the whole batch can
+ * be captured into one CUDA graph from `stream` and replayed.  All items are
+ * validated on the host before anything is enqueued (the first error is
+ * returned).  The auxiliary streams and events are created once per device on
+ * first use (make that first call outside any capture); concurrent batched
+ * calls on one device must be serialised by the caller.
+ */
+typedef struct pp_batch_item {
+    const float *A;
+    const float *Q;
+    int64_t l, m, n, p;
+    int32_t *rho;
+    int64_t *offs;
+    float *Uh_pk, *s_pk, *Vh_pk;
+    float *Ak;            /* may be NULL */
+    pp_report *rep;       /* may be NULL */
+    void *ws;
+    size_t ws_bytes;
+} pp_batch_item;
+
+PP_API pp_status tsvdqII_batched(const pp_batch_item *items, int64_t count, double gamma,
+                                 const pp_opts *opts, void *stream);
+
+/*
  * tsvdqII_noalloc: the same computation as tsvdqII for callers that cannot
  * allocate device memory (no counterpart in the paper; it exists for callers
  * whose device memory belongs to another allocator, latency-critical loops

@@ -49,6 +49,14 @@ class pp_report(ctypes.Structure):
                 ("proj_err2", ctypes.c_double)]
 
 
+class pp_batch_item(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("l", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("rho", ctypes.c_void_p), ("offs", ctypes.c_void_p), ("Uh_pk", ctypes.c_void_p),
+                ("s_pk", ctypes.c_void_p), ("Vh_pk", ctypes.c_void_p), ("Ak", ctypes.c_void_p),
+                ("rep", ctypes.c_void_p), ("ws", ctypes.c_void_p), ("ws_bytes", ctypes.c_size_t)]
+
+
 class pp_hosvd_report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("k1", ctypes.c_int64),
                 ("k2", ctypes.c_int64), ("k", ctypes.c_int64), ("normA2", ctypes.c_double),
@@ -83,6 +91,9 @@ def lib() -> ctypes.CDLL:
                               vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
         for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII"):
             getattr(L, f).restype = i32
+        L.tsvdqII_batched.argtypes = [ctypes.POINTER(pp_batch_item), i64, ctypes.c_double,
+                                      ctypes.POINTER(pp_opts), vp]
+        L.tsvdqII_batched.restype = i32
         L.hosvd_compare.argtypes = [vp, vp, i64, i64, i64, i64, i64, i64, vp, vp,
                                     ctypes.POINTER(pp_opts), vp, sz, vp]
         L.hosvd_compare.restype = i32
@@ -338,3 +349,49 @@ def hosvd_compare(A: torch.Tensor, Q: torch.Tensor, k1: int, k2: int, want_ak: b
                                0 if ws is None else ws.numel(), _stream(stream)), "hosvd_compare")
     raw = bytes(rep.cpu().numpy().tobytes())
     return pp_hosvd_report.from_buffer_copy(raw), Ak
+
+
+class Batch:
+    """Preallocated outputs and workspaces for tsvdqII_batched over a list of
+    (A, Q) device tensors; call() enqueues the whole batch on `stream` (no
+    allocation, so it can be captured into a CUDA graph and replayed)."""
+
+    def __init__(self, pairs, gamma: float, want_ak: bool = False, **opts):
+        self.gamma = float(gamma)
+        self.opts = _opts(**opts)
+        self.outs = []
+        sizes = []
+        for A, Q in pairs:
+            _check_t(A, "A"); _check_t(Q, "Q")
+            n, l, m = A.shape
+            sizes.append(workspace_bytes(PP_OP_TSVDQII, l=l, m=m, n=n, p=Q.shape[1]))
+        offsets, tot = [], 0
+        for nb in sizes:
+            offsets.append(tot)
+            tot += (nb + 1023) // 1024 * 1024
+        dev = pairs[0][0].device
+        self.ws = torch.empty(max(tot, 1), dtype=torch.uint8, device=dev)
+        items = []
+        for (A, Q), off, nb in zip(pairs, offsets, sizes):
+            n, l, m = A.shape
+            p = Q.shape[1]
+            r = min(l, m)
+            o = TsvdqIIOut(torch.empty(p, dtype=torch.int32, device=dev),
+                           torch.empty(p + 1, dtype=torch.int64, device=dev),
+                           torch.empty(p * r * l, dtype=torch.float32, device=dev),
+                           torch.empty(p * r, dtype=torch.float32, device=dev),
+                           torch.empty(p * r * m, dtype=torch.float32, device=dev),
+                           torch.empty((n, l, m), dtype=torch.float32, device=dev) if want_ak else None,
+                           torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev), l, m)
+            self.outs.append(o)
+            items.append(pp_batch_item(A.data_ptr(), Q.data_ptr(), l, m, n, p, o.rho.data_ptr(),
+                                       o.offs.data_ptr(), o.Uh.data_ptr(), o.s.data_ptr(),
+                                       o.Vh.data_ptr(), 0 if o.Ak is None else o.Ak.data_ptr(),
+                                       o.rep.data_ptr(), self.ws.data_ptr() + off, nb))
+        self.pairs = pairs
+        self.items = (pp_batch_item * len(items))(*items)
+
+    def __call__(self, stream=None):
+        _raise(lib().tsvdqII_batched(self.items, len(self.outs), self.gamma,
+                                     ctypes.byref(self.opts), _stream(stream)), "tsvdqII_batched")
+        return self.outs

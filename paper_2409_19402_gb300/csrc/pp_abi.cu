@@ -4,7 +4,10 @@
 // from the host, or synchronises.
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "pp_internal.h"
 
@@ -115,6 +118,35 @@ HosvdWs carve_hosvd(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, int64_
 }
 
 pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUDA; }
+
+// auxiliary streams and fork/join events for tsvdqII_batched, created once per device
+constexpr int AUX_STREAMS = 8;
+constexpr int MAX_DEV = 64;
+struct AuxSet {
+  cudaStream_t s[AUX_STREAMS];
+  cudaEvent_t join[AUX_STREAMS];
+  cudaEvent_t fork;
+  bool ready = false;
+};
+AuxSet g_aux[MAX_DEV];
+std::mutex g_aux_mu;
+
+AuxSet *aux_streams() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return nullptr;
+  std::lock_guard<std::mutex> lock(g_aux_mu);
+  AuxSet &a = g_aux[dev];
+  if (!a.ready) {
+    if (cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    for (int i = 0; i < AUX_STREAMS; ++i) {
+      if (cudaStreamCreateWithFlags(&a.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a.join[i], cudaEventDisableTiming) != cudaSuccess)
+        return nullptr;
+    }
+    a.ready = true;
+  }
+  return &a;
+}
 
 #define PP_TRY(expr)                            \
   do {                                          \
@@ -448,6 +480,47 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
     PP_TRY(pp::launch_report(ra, st));
   }
   stage(5, st);
+  return PP_OK;
+}
+
+pp_status tsvdqII_batched(const pp_batch_item *items, int64_t count, double gamma,
+                          const pp_opts *opts, void *stream) {
+  if (count < 0 || (count > 0 && !items)) return PP_EINVAL;
+  if (!(gamma > 0.0 && gamma <= 1.0)) return PP_EINVAL;
+  for (int64_t i = 0; i < count; ++i) {   // validate everything before enqueuing anything
+    const pp_batch_item &it = items[i];
+    if (!it.A || !it.Q || !it.rho || !it.offs || !it.Uh_pk || !it.s_pk || !it.Vh_pk)
+      return PP_EINVAL;
+    if (bad_dims(it.l, it.m, it.n, it.p)) return PP_ESHAPE;
+    if ((it.l > it.m ? it.l : it.m) > MAX_LONG_SIDE) return PP_ENOSYS;
+    pp_shape sh{it.l, it.m, it.n, it.p, 0, 0};
+    if (pp_status e = check_ws(it.ws, it.ws_bytes, pp_workspace_bytes(PP_OP_TSVDQII, &sh)))
+      return e;
+  }
+  if (count == 0) return PP_OK;
+  AuxSet *aux = aux_streams();
+  if (!aux) return PP_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ns = count < AUX_STREAMS ? (int)count : AUX_STREAMS;
+  PP_TRY(cudaEventRecord(aux->fork, st));
+  for (int k = 0; k < ns; ++k) PP_TRY(cudaStreamWaitEvent(aux->s[k], aux->fork, 0));
+  // largest tensors first (host-side order only), round-robin over the streams
+  std::vector<int64_t> order((size_t)count);
+  for (int64_t i = 0; i < count; ++i) order[(size_t)i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+    return items[x].l * items[x].m * items[x].n > items[y].l * items[y].m * items[y].n;
+  });
+  for (int64_t i = 0; i < count; ++i) {
+    const pp_batch_item &it = items[order[(size_t)i]];
+    if (pp_status e = tsvdqII(it.A, it.Q, it.l, it.m, it.n, it.p, gamma, it.rho, it.offs,
+                              it.Uh_pk, it.s_pk, it.Vh_pk, it.Ak, it.rep, opts, it.ws,
+                              it.ws_bytes, aux->s[i % ns]))
+      return e;
+  }
+  for (int k = 0; k < ns; ++k) {
+    PP_TRY(cudaEventRecord(aux->join[k], aux->s[k]));
+    PP_TRY(cudaStreamWaitEvent(st, aux->join[k], 0));
+  }
   return PP_OK;
 }
 

@@ -136,7 +136,7 @@ def batched(seed: int = 3, count: int = 64, noise_std: float = 1e-3, rank: int =
         A = np.einsum("abc,ia,jb,tc->tij", G, U1, U2, U3, optimize=True)
         A /= math.sqrt(float((A ** 2).mean()))
         A += noise_std * rng.standard_normal(A.shape)
-        out.append((A.astype(np.float32), p))
+        out.append((np.ascontiguousarray(A, dtype=np.float32), p))
     return out
 
 
