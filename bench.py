@@ -353,6 +353,11 @@ def run_ours(args):
               "value": L * M * N / (ms_pn / 1e3), "err2": rpn.err2, "err2_target": err_target,
               "kappa": int(rpn.kappa), "speedup_p_lt_n": ms_pn / ms_per_step}
 
+    # ---------------- batched uneven workload (64 tensors): eager fork/join vs CUDA graph
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = run_batched(args, torch, binding, stream, dev)
+
     # ---------------- end to end through host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -369,7 +374,46 @@ def run_ours(args):
                "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
                "seconds": dt}
     return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-                  per_step_launches, clk, t_wall, dist, tuned)
+                  per_step_launches, clk, t_wall, dist, tuned, batched)
+
+
+def run_batched(args, torch, binding, stream, dev):
+    """64 uneven Tucker-rank-10 tensors (tSVDQII, gamma = 0.95, Q = U3 per tensor):
+    one tsvdqII_batched call per step, timed eagerly and as a replayed CUDA graph.
+    The inputs (1.3 GB) exceed L2, so no flush is needed between steps."""
+    from paper_2409_19402_gb300 import inputs
+    items = inputs.batched()
+    pairs = [(torch.from_numpy(A).to(dev), torch.from_numpy(inputs.u3_q(A, p)).to(dev))
+             for A, p in items]
+    entries = sum(int(A.numel()) for A, _ in pairs)
+    B = binding.Batch(pairs, 0.95)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    launches0 = binding.kernel_launches()
+    ms_eager = timed(lambda: B(stream))
+    per_call = (binding.kernel_launches() - launches0) / (args.steps + args.warmup)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        B(stream)
+    ms_graph = timed(lambda: g.replay())
+    reps = [o.report() for o in B.outs]
+    return {"tensors": len(pairs), "entries": entries, "gamma": 0.95,
+            "ms_eager": ms_eager, "ms_graph": ms_graph,
+            "value_eager": entries / (ms_eager / 1e3), "value_graph": entries / (ms_graph / 1e3),
+            "unit": UNIT, "kernels_per_call": per_call,
+            "status_ok": all(r.status == 0 for r in reps),
+            "max_sweeps": max(r.sweeps for r in reps)}
 
 
 def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
@@ -414,7 +458,7 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-           per_step_launches, clk, t_wall, dist, tuned=None):
+           per_step_launches, clk, t_wall, dist, tuned=None, batched=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -430,6 +474,7 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
             "roofline": roofline,
             "stages": stages,
             "pn_compare": pn,
+            "batched_64": batched,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(round(per_step_launches * args.steps)),
@@ -451,6 +496,7 @@ def main():
     ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-tensor batched run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
