@@ -24,6 +24,9 @@ Function -> passage it follows:
   hosvd              truncated HOSVD of Sec. 4.2
   dct_q, householder_q, u3_q   transformation matrices of Sec. 5.1.1
   relative_error, compression_ratio   metrics RE and CR of Sec. 5.1.2
+  qprod_grad         gradient of 1/2 |A *Q B - T|^2 w.r.t. A, B and Q (chain rule
+                     through Def. 3.1; Q gradient also projected on the Stiefel
+                     tangent space)
 """
 from __future__ import annotations
 
@@ -76,6 +79,8 @@ def _L():
         lib.or_mode_gram.argtypes = [dp, i64, i64, i64, ctypes.c_int, dp]
         lib.or_hosvd.argtypes = [dp, i64, i64, i64, i64, i64, dp, i64, dp, dp]
         lib.or_dct_q.argtypes = [i64, i64, dp]
+        lib.or_qprod_grad.argtypes = [dp, dp, dp, dp, i64, i64, i64, i64, i64, dp, dp, dp, dp, dp]
+        lib.or_qprod_grad.restype = ctypes.c_int
         lib.or_householder_q.argtypes = [dp, i64, i64, dp]
         for f in ("or_qprod", "or_mprod", "or_svd_jacobi", "or_tsvdq", "or_select_energy",
                   "or_tsvdqII", "or_sym_eig_jacobi", "or_hosvd", "or_householder_q"):
@@ -335,3 +340,17 @@ def storage_hosvd(n1: int, n2: int, n3: int, k1: int, k2: int, k3: int) -> int:
 def compression_ratio(n1: int, n2: int, n3: int, st_approx: int, st_q: int) -> float:
     """CR = st[A] / (st[A~] + st[Q]) with st[A] = n1 n2 n3 (Sec. 5.1.2)."""
     return float(n1 * n2 * n3) / float(st_approx + st_q)
+
+
+def qprod_grad(A, B, Q, T):
+    """Gradient of L = 1/2 |A *Q B - T|_F^2.  Returns (L, dA, dB, dQ_euclid, dQ_stiefel)."""
+    A, B, Q, T = _f64(A), _f64(B), _f64(Q), _f64(T)
+    n, n1, m = A.shape
+    n2 = B.shape[2]
+    p = Q.shape[1]
+    dA, dB = np.empty_like(A), np.empty_like(B)
+    dQE, dQ = np.empty((n, p)), np.empty((n, p))
+    loss = ctypes.c_double(0)
+    _check(_L().or_qprod_grad(_p(A), _p(B), _p(Q), _p(T), n1, m, n2, n, p, _p(dA), _p(dB),
+                              _p(dQE), _p(dQ), ctypes.byref(loss)), "qprod_grad")
+    return loss.value, dA, dB, dQE, dQ

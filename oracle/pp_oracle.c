@@ -27,6 +27,10 @@
  *   or_sym_eig_jacobi   symmetric eigensolver for the mode-i factor matrices
  *   or_hosvd            truncated HOSVD of Sec. 4.2
  *   or_dct_q, or_householder_q   transformation matrices of Sec. 5.1.1
+ *   or_qprod_grad       gradient of L = 1/2 |A *Q B - T|_F^2 with respect to A, B
+ *                       and Q (Euclidean and projected on the tangent space of
+ *                       the Stiefel manifold St_{n,p} of Sec. 3), by the chain
+ *                       rule through the three steps of Def. 3.1
  */
 #include <math.h>
 #include <stdint.h>
@@ -771,4 +775,79 @@ int or_householder_q(const double *X, i64 n, i64 p, double *Q)
     }
     free(R); free(H); free(v);
     return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient of L = 1/2 |C - T|_F^2 with C = A *Q B (Def. 3.1), A n1 x m x n,
+ * B m x n2 x n, Q n x p, by the chain rule through the three steps:
+ *   A-hat = A x_3 Q^T, B-hat = B x_3 Q^T, C-hat = A-hat ^ B-hat, C = C-hat x_3 Q.
+ * With G = C - T:
+ *   G-hat = G x_3 Q^T                         (dL/dC-hat, since C_(3) = Q C-hat_(3))
+ *   dA-hat_t = G-hat_t B-hat_t^T, dB-hat_t = A-hat_t^T G-hat_t
+ *   dA = dA-hat x_3 Q, dB = dB-hat x_3 Q      (A-hat_(3) = Q^T A_(3))
+ *   dQ_E = G_(3) C-hat_(3)^T + A_(3) dA-hat_(3)^T + B_(3) dB-hat_(3)^T
+ *   dQ = dQ_E - Q sym(Q^T dQ_E), sym(M) = (M + M^T)/2 (tangent projection at Q)
+ * Outputs dA (n x n1 x m storage), dB, dQE and dQ (n x p); returns L in *loss. */
+int or_qprod_grad(const double *A, const double *B, const double *Q, const double *T,
+                  i64 n1, i64 m, i64 n2, i64 n, i64 p, double *dA, double *dB,
+                  double *dQE, double *dQ, double *loss)
+{
+    double *Qt = malloc(sizeof(double) * p * n);
+    double *Ah = malloc(sizeof(double) * p * n1 * m), *Bh = malloc(sizeof(double) * p * m * n2);
+    double *Ch = malloc(sizeof(double) * p * n1 * n2), *C = malloc(sizeof(double) * n * n1 * n2);
+    double *G = malloc(sizeof(double) * n * n1 * n2), *Gh = malloc(sizeof(double) * p * n1 * n2);
+    double *dAh = malloc(sizeof(double) * p * n1 * m), *dBh = malloc(sizeof(double) * p * m * n2);
+    double *S = malloc(sizeof(double) * p * p);
+    int st = OR_OK;
+    if (!Qt || !Ah || !Bh || !Ch || !C || !G || !Gh || !dAh || !dBh || !S) { st = OR_ENOMEM; goto out; }
+    transpose(Q, n, p, Qt);
+    or_mode3(A, n1, m, n, Qt, p, Ah);
+    or_mode3(B, m, n2, n, Qt, p, Bh);
+    or_facewise(Ah, Bh, n1, m, n2, p, Ch);
+    or_mode3(Ch, n1, n2, p, Q, n, C);
+    {
+        double l2 = 0.0;
+        for (i64 e = 0; e < n * n1 * n2; ++e) { G[e] = C[e] - T[e]; l2 += G[e] * G[e]; }
+        *loss = 0.5 * l2;
+    }
+    or_mode3(G, n1, n2, n, Qt, p, Gh);
+    for (i64 t = 0; t < p; ++t) {
+        for (i64 i = 0; i < n1; ++i)          /* dA-hat_t = G-hat_t B-hat_t^T */
+            for (i64 l = 0; l < m; ++l) {
+                double acc = 0.0;
+                for (i64 j = 0; j < n2; ++j) acc += Gh[TIDX(i, j, t, n1, n2)] * Bh[TIDX(l, j, t, m, n2)];
+                dAh[TIDX(i, l, t, n1, m)] = acc;
+            }
+        for (i64 l = 0; l < m; ++l)           /* dB-hat_t = A-hat_t^T G-hat_t */
+            for (i64 j = 0; j < n2; ++j) {
+                double acc = 0.0;
+                for (i64 i = 0; i < n1; ++i) acc += Ah[TIDX(i, l, t, n1, m)] * Gh[TIDX(i, j, t, n1, n2)];
+                dBh[TIDX(l, j, t, m, n2)] = acc;
+            }
+    }
+    or_mode3(dAh, n1, m, p, Q, n, dA);
+    or_mode3(dBh, m, n2, p, Q, n, dB);
+    for (i64 s = 0; s < n; ++s)               /* dQ_E(s, t) */
+        for (i64 t = 0; t < p; ++t) {
+            double acc = 0.0;
+            for (i64 e = 0; e < n1 * n2; ++e) acc += G[s * n1 * n2 + e] * Ch[t * n1 * n2 + e];
+            for (i64 e = 0; e < n1 * m; ++e) acc += A[s * n1 * m + e] * dAh[t * n1 * m + e];
+            for (i64 e = 0; e < m * n2; ++e) acc += B[s * m * n2 + e] * dBh[t * m * n2 + e];
+            dQE[s * p + t] = acc;
+        }
+    for (i64 a = 0; a < p; ++a)               /* S = Q^T dQ_E */
+        for (i64 b = 0; b < p; ++b) {
+            double acc = 0.0;
+            for (i64 s = 0; s < n; ++s) acc += Q[s * p + a] * dQE[s * p + b];
+            S[a * p + b] = acc;
+        }
+    for (i64 s = 0; s < n; ++s)
+        for (i64 t = 0; t < p; ++t) {
+            double acc = 0.0;
+            for (i64 a = 0; a < p; ++a) acc += Q[s * p + a] * 0.5 * (S[a * p + t] + S[t * p + a]);
+            dQ[s * p + t] = dQE[s * p + t] - acc;
+        }
+out:
+    free(Qt); free(Ah); free(Bh); free(Ch); free(C); free(G); free(Gh); free(dAh); free(dBh); free(S);
+    return st;
 }

@@ -463,3 +463,38 @@ def test_tiny_config_dct_tsvdq():
         np.testing.assert_allclose(s[t], np.linalg.svd(Ah[t], compute_uv=False)[:3], rtol=1e-12)
     C = oracle.qprod(A, B, Q)
     assert C.shape == (16, 32, 20)
+
+
+def test_qprod_gradient_matches_central_differences():
+    """The oracle's analytic gradient of 1/2 |A *Q B - T|^2 (chain rule through
+    Def. 3.1) against FP64 central finite differences, on the 16x12x32, p = 8
+    instance (B 12 x 10 x 32); the Stiefel gradient is the tangent projection of
+    the Euclidean one and is orthogonal to Q's normal space."""
+    rng = np.random.default_rng(4)
+    n, n1, m, n2, p = 32, 16, 12, 10, 8
+    A = rng.standard_normal((n, n1, m)) / 4
+    B = rng.standard_normal((n, m, n2)) / 4
+    Q = _rand_q(n, p)
+    T = rng.standard_normal((n, n1, n2))
+    L0, dA, dB, dQE, dQ = oracle.qprod_grad(A, B, Q, T)
+    f = lambda A_, B_, Q_: 0.5 * ((oracle.qprod(A_, B_, Q_) - T) ** 2).sum()
+    assert L0 == pytest.approx(f(A, B, Q), rel=1e-12)
+    # L is quadratic in A and in B (central differences exact up to rounding: large h)
+    # and of degree 6 in Q (O(h^2) truncation: small h)
+    steps = {"A": 1e-2, "B": 1e-2, "Q": 1e-5}
+    for _ in range(12):
+        for which, X, dX in (("A", A, dA), ("B", B, dB), ("Q", Q, dQE)):
+            h = steps[which]
+            idx = tuple(rng.integers(0, s) for s in X.shape)
+            Xp, Xm = X.copy(), X.copy()
+            Xp[idx] += h
+            Xm[idx] -= h
+            args_p = {"A": (Xp, B, Q), "B": (A, Xp, Q), "Q": (A, B, Xp)}[which]
+            args_m = {"A": (Xm, B, Q), "B": (A, Xm, Q), "Q": (A, B, Xm)}[which]
+            fd = (f(*args_p) - f(*args_m)) / (2 * h)
+            assert fd == pytest.approx(dX[idx], rel=1e-6, abs=1e-8), (which, idx)
+    # tangent projection: Q^T dQ is skew-symmetric, and dQ = dQE - Q sym(Q^T dQE)
+    S = Q.T @ dQ
+    np.testing.assert_allclose(S + S.T, 0.0, atol=1e-10)
+    M = Q.T @ dQE
+    np.testing.assert_allclose(dQ, dQE - Q @ (0.5 * (M + M.T)), atol=1e-12)
