@@ -141,21 +141,35 @@ def make_inputs():
 
 
 # ------------------------------------------------------------------ reference arm
+REF_BUDGET_S = 150.0
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     import oracle
     A, Qp, _ = make_inputs()
-    for _ in range(args.warmup):
-        oracle.tsvdqII(A, Qp, GAMMA)
+    # Each step is a bounded sample: the whole tensor when (steps + warmup) full
+    # oracle steps fit REF_BUDGET_S, else the leading rows of every frame (a
+    # smaller tSVDQII problem of the same kind, same Q and gamma).
+    t0 = time.perf_counter()
+    oracle.tsvdqII(A, Qp, GAMMA)                      # first warm-up step, full size
+    t_full = time.perf_counter() - t0
+    per_step = REF_BUDGET_S / max(1, args.steps + args.warmup)
+    rows = L if t_full <= per_step else max(8, int(L * per_step / t_full))
+    As = np.ascontiguousarray(A[:, :rows, :])
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.tsvdqII(As, Qp, GAMMA)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.tsvdqII(A, Qp, GAMMA)
+        oracle.tsvdqII(As, Qp, GAMMA)
         times.append(time.perf_counter() - t0)
     total = sum(times)
-    value = L * M * N * args.steps / total
+    value = rows * M * N * args.steps / total
+    sample = ("each step: one full oracle tsvdqII of the workload" if rows == L else
+              f"each step: oracle tsvdqII of the leading {rows} of {L} rows of every frame "
+              f"({rows}x{M}x{N}, same Q and gamma)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -163,7 +177,7 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l": L, "m": M, "n": N, "p": P, "gamma": GAMMA},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: one full oracle tsvdqII of the workload"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -358,6 +372,11 @@ def run_ours(args):
     if world == 1 and not args.no_batched:
         batched = run_batched(args, torch, binding, stream, dev)
 
+    # ---------------- differentiable projected product (config: W 256x256x512, X 256x64x512)
+    diff = None
+    if world == 1 and not args.no_diff:
+        diff = run_diff(args, torch, stream, dev)
+
     # ---------------- end to end through host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -374,7 +393,46 @@ def run_ours(args):
                "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
                "seconds": dt}
     return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-                  per_step_launches, clk, t_wall, dist, tuned, batched)
+                  per_step_launches, clk, t_wall, dist, tuned, batched, diff)
+
+
+def run_diff(args, torch, stream, dev):
+    """One training step of the projected-product layer Y = W *Q X (forward, loss
+    1/2 |Y - T|^2, hand-written backward with the Stiefel-projected Q gradient)
+    at W 256x256x512, X 256x64x512 (BF16 values, computed in FP32), Q 512x64."""
+    from paper_2409_19402_gb300 import autograd as ag
+    g = torch.Generator(device="cpu").manual_seed(4)
+    W = (torch.randn((512, 256, 256), generator=g) / 16).to(torch.bfloat16).float().to(dev)
+    X = (torch.randn((512, 256, 64), generator=g) / 16).to(torch.bfloat16).float().to(dev)
+    Q = torch.linalg.qr(torch.randn((512, 64), generator=g, dtype=torch.float64))[0].float().to(dev)
+    Ws = (torch.randn((512, 256, 256), generator=g) / 16).to(dev)
+    Qs = torch.linalg.qr(torch.randn((512, 64), generator=g, dtype=torch.float64))[0].float().to(dev)
+    with torch.no_grad():
+        T = ag.qprod(Ws, X, Qs)
+    W.requires_grad_(); X.requires_grad_(); Q.requires_grad_()
+
+    def step():
+        W.grad = X.grad = Q.grad = None
+        loss = 0.5 * ((ag.qprod(W, X, Q) - T) ** 2).sum()
+        loss.backward()
+        return loss
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            loss = step()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    n, n1, m, n2, p = 512, 256, 256, 64, 64
+    flops = 2.0 * (n * p * (n1 * m + m * n2) + p * n1 * m * n2 + n * p * n1 * n2)  # forward
+    return {"shapes": "W 256x256x512, X 256x64x512, Q 512x64", "ms_fwd_bwd": ms,
+            "loss": float(loss.detach()), "forward_flops": flops,
+            "note": "includes the torch loss/residual ops; all products in the library"}
 
 
 def run_batched(args, torch, binding, stream, dev):
@@ -458,7 +516,7 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-           per_step_launches, clk, t_wall, dist, tuned=None, batched=None):
+           per_step_launches, clk, t_wall, dist, tuned=None, batched=None, diff=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -475,6 +533,7 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
             "stages": stages,
             "pn_compare": pn,
             "batched_64": batched,
+            "diff_step": diff,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(round(per_step_launches * args.steps)),
@@ -490,13 +549,14 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-tensor batched run")
+    ap.add_argument("--no-diff", action="store_true", help="skip the differentiation step run")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

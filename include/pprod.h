@@ -76,7 +76,8 @@ typedef enum pp_op {
     PP_OP_PPROD = 2,
     PP_OP_TSVDQ = 3,
     PP_OP_TSVDQII = 4,
-    PP_OP_HOSVD = 5
+    PP_OP_HOSVD = 5,
+    PP_OP_PPROD_BWD = 6
 } pp_op;
 
 /* Problem sizes for pp_workspace_bytes.  Fields an op does not use are
@@ -161,6 +162,23 @@ PP_API pp_status pprod_facewise(const float *Ah, const float *Bh, int64_t n1, in
 PP_API pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1,
                 int64_t m, int64_t n2, int64_t n, int64_t p, float *C,
                 void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Backward of the projected product C = A *Q B (Def. 3.1) for a loss L with
+ * G = dL/dC, by the chain rule through its three steps (the transform-domain
+ * tensors A-hat, B-hat, C-hat are recomputed, not stored):
+ *   G-hat = G x_3 Q^T;  dA-hat_t = G-hat_t B-hat_t^T;  dB-hat_t = A-hat_t^T G-hat_t
+ *   dA = dA-hat x_3 Q;  dB = dB-hat x_3 Q
+ *   dQ_E = G_(3) C-hat_(3)^T + A_(3) dA-hat_(3)^T + B_(3) dB-hat_(3)^T   (n x p)
+ *   dQ   = dQ_E - Q sym(Q^T dQ_E)  (projection on the tangent space of St_{n,p})
+ * Sizes as in pprod; G, dA, dB have the shapes of C, A, B.  dQ_euclid and dQ
+ * (n x p) may each be NULL.  Workspace: pp_workspace_bytes(PP_OP_PPROD_BWD,
+ * {l = n1, m, n, p, n2}).
+ */
+PP_API pp_status pprod_backward(const float *A, const float *B, const float *Q, const float *G,
+                                int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p,
+                                float *dA, float *dB, float *dQ_euclid, float *dQ,
+                                void *ws, size_t ws_bytes, void *stream);
 
 /*
  * Truncated *Q-SVD (Alg. 4.1; Def. 4.1; error terms of Thm. 4.2).

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpprod.so")
 PP_OK, PP_EINVAL, PP_ESHAPE, PP_ENOTORTHO, PP_ENONFINITE, PP_ENOCONV = 0, 1, 2, 3, 4, 5
 PP_ETIMEOUT, PP_EWORKSPACE, PP_ECUDA, PP_ENOSYS = 6, 7, 8, 9
 PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII, PP_OP_HOSVD = 0, 1, 2, 3, 4, 5
+PP_OP_PPROD_BWD = 6
 
 
 class PPError(RuntimeError):
@@ -91,6 +92,9 @@ def lib() -> ctypes.CDLL:
                               vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
         for f in ("pprod_mode3", "pprod_facewise", "pprod", "tsvdq_trunc", "tsvdqII"):
             getattr(L, f).restype = i32
+        L.pprod_backward.argtypes = [vp, vp, vp, vp, i64, i64, i64, i64, i64, vp, vp, vp, vp,
+                                     vp, sz, vp]
+        L.pprod_backward.restype = i32
         L.tsvdqII_batched.argtypes = [ctypes.POINTER(pp_batch_item), i64, ctypes.c_double,
                                       ctypes.POINTER(pp_opts), vp]
         L.tsvdqII_batched.restype = i32
@@ -218,6 +222,26 @@ def pprod(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, out=None, ws=None, 
     _raise(lib().pprod(_ptr(A), _ptr(B), _ptr(Q), n1, m, n2, n, p, _ptr(out), _ptr(ws),
                        0 if ws is None else ws.numel(), _stream(stream)), "pprod")
     return out
+
+
+def pprod_backward(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, G: torch.Tensor,
+                   want_euclid: bool = False, ws=None, stream=None):
+    """Backward of A *Q B for dL/dC = G: returns (dA, dB, dQ_stiefel, dQ_euclid or None)."""
+    for t, nm in ((A, "A"), (B, "B"), (Q, "Q"), (G, "G")):
+        _check_t(t, nm)
+    n, n1, m = A.shape
+    n2 = B.shape[2]
+    p = Q.shape[1]
+    dA, dB = torch.empty_like(A), torch.empty_like(B)
+    dQ = torch.empty_like(Q)
+    dQE = torch.empty_like(Q) if want_euclid else None
+    need = workspace_bytes(PP_OP_PPROD_BWD, l=n1, m=m, n=n, p=p, n2=n2)
+    if ws is None:
+        ws = workspace(need, A.device)
+    _raise(lib().pprod_backward(_ptr(A), _ptr(B), _ptr(Q), _ptr(G), n1, m, n2, n, p, _ptr(dA),
+                                _ptr(dB), _ptr(dQE), _ptr(dQ), _ptr(ws),
+                                0 if ws is None else ws.numel(), _stream(stream)), "pprod_backward")
+    return dA, dB, dQ, dQE
 
 
 @dataclass

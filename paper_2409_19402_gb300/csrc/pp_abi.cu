@@ -119,6 +119,28 @@ HosvdWs carve_hosvd(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, int64_
 
 pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUDA; }
 
+struct BwdWs {
+  float *Ah, *Bh, *Ch, *Gh, *dAh, *dBh, *part, *dQE, *Sm;
+};
+
+BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p) {
+  BwdWs w;
+  w.Ah = c.take<float>(p * n1 * m);
+  w.Bh = c.take<float>(p * m * n2);
+  w.Ch = c.take<float>(p * n1 * n2);
+  w.Gh = c.take<float>(p * n1 * n2);
+  w.dAh = c.take<float>(p * n1 * m);
+  w.dBh = c.take<float>(p * m * n2);
+  int64_t z = pp::nt_splits(n, p, n1 * n2);
+  const int64_t z2 = pp::nt_splits(n, p, n1 * m), z3 = pp::nt_splits(n, p, m * n2);
+  if (z2 > z) z = z2;
+  if (z3 > z) z = z3;
+  w.part = c.take<float>(z * n * p);
+  w.dQE = c.take<float>(n * p);
+  w.Sm = c.take<float>(p * p);
+  return w;
+}
+
 // auxiliary streams and fork/join events for tsvdqII_batched, created once per device
 constexpr int AUX_STREAMS = 8;
 constexpr int MAX_DEV = 64;
@@ -289,6 +311,12 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
       if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
       carve_decomp(c, sh->l, sh->m, sh->n, sh->p, op == PP_OP_TSVDQII);
       return c.off;
+    case PP_OP_PPROD_BWD:
+      if (bad_dims(sh->l, sh->m, sh->n, sh->p) || bad_dims(sh->m, sh->n2, sh->n, sh->p) ||
+          bad_dims(sh->l, sh->n2, sh->n, sh->p))
+        return 0;
+      carve_bwd(c, sh->l, sh->m, sh->n2, sh->n, sh->p);
+      return c.off;
     case PP_OP_HOSVD:
       if (bad_dims(sh->l, sh->m, sh->n, sh->p) || sh->k < 1 || sh->k > sh->l || sh->n2 < 1 ||
           sh->n2 > sh->m)
@@ -344,6 +372,49 @@ pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1, int6
   PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st));
   PP_TRY(pp::launch_mode3_tc(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, nullptr,
                              nullptr, nullptr, nullptr, st));
+  return PP_OK;
+}
+
+pp_status pprod_backward(const float *A, const float *B, const float *Q, const float *G,
+                         int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p, float *dA,
+                         float *dB, float *dQ_euclid, float *dQ, void *ws, size_t ws_bytes,
+                         void *stream) {
+  if (!A || !B || !Q || !G || !dA || !dB) return PP_EINVAL;
+  if (bad_dims(n1, m, n, p) || bad_dims(m, n2, n, p) || bad_dims(n1, n2, n, p) || p > 65535)
+    return PP_ESHAPE;
+  pp_shape sh{n1, m, n, p, 0, n2};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_PPROD_BWD, &sh))) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const BwdWs w = carve_bwd(c, n1, m, n2, n, p);
+  auto fwd = [&](const float *X, int64_t pix, float *Y) {   // Y = X x_3 Q^T
+    return pp::launch_mode3_tc(Q, 1, p, X, Y, p, n, pix, nullptr, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, st);
+  };
+  auto back = [&](const float *X, int64_t pix, float *Y) {  // Y = X x_3 Q
+    return pp::launch_mode3_tc(Q, p, 1, X, Y, n, p, pix, nullptr, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, st);
+  };
+  // recompute the transform-domain operands
+  PP_TRY(fwd(A, n1 * m, w.Ah));
+  PP_TRY(fwd(B, m * n2, w.Bh));
+  PP_TRY(pp::launch_facewise_gemm(w.Ah, w.Bh, w.Ch, n1, m, n2, p, st));
+  PP_TRY(fwd(G, n1 * n2, w.Gh));
+  // dA-hat_t (n1 x m) = G-hat_t (n1 x n2) B-hat_t^T: X(c = j, n = l) = B-hat_t[l*n2 + j]
+  PP_TRY(pp::launch_batched_gemm(w.Gh, n2, 1, n1 * n2, w.Bh, m * n2, w.dAh, n1 * m, n1, n2, m, p,
+                                 st, 1, n2));
+  // dB-hat_t (m x n2) = A-hat_t^T (m x n1) G-hat_t: M(r = l, c = i) = A-hat_t[i*m + l]
+  PP_TRY(pp::launch_batched_gemm(w.Ah, 1, m, n1 * m, w.Gh, n1 * n2, w.dBh, m * n2, m, n1, n2, p,
+                                 st));
+  PP_TRY(back(w.dAh, n1 * m, dA));
+  PP_TRY(back(w.dBh, m * n2, dB));
+  if (dQ_euclid || dQ) {
+    float *dQE = dQ_euclid ? dQ_euclid : w.dQE;
+    PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st));
+    PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st));
+    PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st));
+    if (dQ) PP_TRY(pp::launch_stiefel(Q, dQE, n, p, w.Sm, dQ, st));
+  }
   return PP_OK;
 }
 

@@ -22,6 +22,7 @@ constexpr int BM = 64;   // output slices per CTA
 constexpr int BN = 128;  // pixels per CTA
 constexpr int BK = 16;   // contraction step
 constexpr int NT = 256;  // threads per CTA
+constexpr int64_t NUM_SMS_GEMM = 152;
 
 __device__ __forceinline__ double block_sum_double(double v, double *red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -38,9 +39,10 @@ __device__ __forceinline__ double block_sum_double(double v, double *red) {
 // Y[z] (P x N) = M[z] (P x S) * X[z] (S x N); M(r, c) = Qm[z*sMz + r*sr + c*sc].
 __global__ void __launch_bounds__(NT) gemm_tile_kernel(
     const float *__restrict__ Qm, int64_t sr, int64_t sc, int64_t sMz,
-    const float *__restrict__ X, int64_t sXz, float *__restrict__ Y, int64_t sYz, int64_t P,
-    int64_t S, int64_t N, const float *__restrict__ Aref, double *__restrict__ errp,
-    double *__restrict__ xpart, double *__restrict__ ypart) {
+    const float *__restrict__ X, int64_t sXz, int64_t sxc, int64_t sxn, float *__restrict__ Y,
+    int64_t sYz, int64_t P, int64_t S, int64_t N, const float *__restrict__ Aref,
+    double *__restrict__ errp, double *__restrict__ xpart, double *__restrict__ ypart) {
+  // X(c, n) = X[z*sXz + c*sxc + n*sxn] (row-major: sxc = N, sxn = 1)
   // Y may be nullptr (only the error partials are produced); xpart / ypart may be
   // nullptr.  xpart[blockIdx.x] (CTAs of the first row tile only) and
   // ypart[CTA] receive the FP64 sums of squares of the X tiles and Y tile.
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(NT) gemm_tile_kernel(
     for (int e = tid; e < BK * BN; e += NT) {
       const int cc = e / BN, nn = e % BN;
       const int64_t c = c0 + cc, n = n0 + nn;
-      const float v = (c < S && n < N) ? X[c * N + n] : 0.f;
+      const float v = (c < S && n < N) ? X[c * sxc + n * sxn] : 0.f;
       Xs[cc][nn] = v;
       if (do_x) xs += (double)v * v;
     }
@@ -141,18 +143,144 @@ cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const flo
   if (n_partials) *n_partials = (int)(grid.x * grid.y);
   if (n_xpart) *n_xpart = (int)grid.x;
   count_launch(1);
-  gemm_tile_kernel<<<grid, NT, 0, st>>>(Qm, sr, sc, 0, X, 0, Y, 0, P, S, N, Aref,
+  gemm_tile_kernel<<<grid, NT, 0, st>>>(Qm, sr, sc, 0, X, 0, N, 1, Y, 0, P, S, N, Aref,
                                         err_partials, xpart, ypart);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
                                 const float *X, int64_t sXz, float *Y, int64_t sYz, int64_t P,
-                                int64_t S, int64_t N, int64_t batch, cudaStream_t st) {
+                                int64_t S, int64_t N, int64_t batch, cudaStream_t st,
+                                int64_t sxc, int64_t sxn) {
+  if (sxc < 0) { sxc = N; sxn = 1; }
   const dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((P + BM - 1) / BM), (unsigned)batch);
   count_launch(1);
-  gemm_tile_kernel<<<grid, NT, 0, st>>>(Mm, sr, sc, sMz, X, sXz, Y, sYz, P, S, N, nullptr,
-                                        nullptr, nullptr, nullptr);
+  gemm_tile_kernel<<<grid, NT, 0, st>>>(Mm, sr, sc, sMz, X, sXz, sxc, sxn, Y, sYz, P, S, N,
+                                        nullptr, nullptr, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// ---------------------------------------------------------------- A B^T, split over K
+// part[z] (R x S) = A[:, kz] B[:, kz]^T over the z-th chunk of the common dimension K;
+// A (R x K) and B (S x K) row-major.  Tiles 64 x 64, 256 threads.
+__global__ void __launch_bounds__(256) nt_partial_kernel(const float *__restrict__ A,
+                                                         const float *__restrict__ B, int64_t R,
+                                                         int64_t S, int64_t K, int64_t kchunk,
+                                                         float *__restrict__ part) {
+  __shared__ float As[16][64 + 1], Bs[16][64 + 1];
+  const int64_t r0 = (int64_t)blockIdx.y * 64, s0 = (int64_t)blockIdx.x * 64;
+  const int64_t k0 = (int64_t)blockIdx.z * kchunk, k1 = min(K, k0 + kchunk);
+  const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
+  float acc[4][4] = {};
+  for (int64_t kb = k0; kb < k1; kb += 16) {
+    for (int e = tid; e < 64 * 16; e += 256) {
+      const int kk = e % 16, rr = e / 16;
+      const int64_t k = kb + kk;
+      As[kk][rr] = (k < k1 && r0 + rr < R) ? A[(r0 + rr) * K + k] : 0.f;
+      Bs[kk][rr] = (k < k1 && s0 + rr < S) ? B[(s0 + rr) * K + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) { a[q] = As[kk][ti + 16 * q]; b[q] = Bs[kk][tj + 16 * q]; }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[q][c] = fmaf(a[q], b[c], acc[q][c]);
+    }
+    __syncthreads();
+  }
+  float *P = part + (int64_t)blockIdx.z * R * S;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t r = r0 + ti + 16 * q;
+    if (r >= R) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int64_t s = s0 + tj + 16 * c;
+      if (s < S) P[r * S + s] = acc[q][c];
+    }
+  }
+}
+
+// out (R x S) (+)= sum over z of part[z], in z order
+__global__ void sum_parts_kernel(const float *__restrict__ part, int64_t count, int64_t nz,
+                                 float *__restrict__ out, int accumulate) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    float s = accumulate ? out[e] : 0.f;
+    for (int64_t z = 0; z < nz; ++z) s += part[z * count + e];
+    out[e] = s;
+  }
+}
+
+// S (p x p) = Q^T D; then D <- D - Q sym(S) (tangent projection at Q on St_{n,p})
+__global__ void qtd_kernel(const float *__restrict__ Q, const float *__restrict__ D, int64_t n,
+                           int64_t p, float *__restrict__ Sm) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < p * p;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / p, b = e % p;
+    float s = 0.f;
+    for (int64_t i = 0; i < n; ++i) s = fmaf(Q[i * p + a], D[i * p + b], s);
+    Sm[e] = s;
+  }
+}
+
+__global__ void stiefel_kernel(const float *__restrict__ Q, const float *__restrict__ D,
+                               const float *__restrict__ Sm, int64_t n, int64_t p,
+                               float *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * p;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / p, b = e % p;
+    float s = 0.f;
+    for (int64_t a = 0; a < p; ++a) s = fmaf(Q[i * p + a], 0.5f * (Sm[a * p + b] + Sm[b * p + a]), s);
+    out[e] = D[e] - s;
+  }
+}
+
+}  // namespace
+
+int64_t nt_splits(int64_t R, int64_t S, int64_t K) {
+  const int64_t tiles = ((R + 63) / 64) * ((S + 63) / 64);
+  int64_t z = (NUM_SMS_GEMM * 3 + tiles - 1) / tiles;
+  const int64_t zmax = (K + 255) / 256;   // at least 256 of K per split
+  if (z > zmax) z = zmax;
+  return z < 1 ? 1 : z;
+}
+
+cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
+                                 float *part, float *out, int accumulate, cudaStream_t st) {
+  const int64_t nz = nt_splits(R, S, K);
+  const int64_t kchunk = (K + nz - 1) / nz;
+  const dim3 grid((unsigned)((S + 63) / 64), (unsigned)((R + 63) / 64), (unsigned)nz);
+  count_launch(1);
+  nt_partial_kernel<<<grid, 256, 0, st>>>(A, B, R, S, K, kchunk, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t count = R * S;
+  int blocks = (int)((count + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  count_launch(1);
+  sum_parts_kernel<<<blocks, 256, 0, st>>>(part, count, nz, out, accumulate);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p, float *Sm,
+                           float *out, cudaStream_t st) {
+  int b1 = (int)((p * p + 255) / 256);
+  if (b1 > 4096) b1 = 4096;
+  count_launch(1);
+  qtd_kernel<<<b1, 256, 0, st>>>(Q, D, n, p, Sm);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int b2 = (int)((n * p + 255) / 256);
+  if (b2 > 4096) b2 = 4096;
+  count_launch(1);
+  stiefel_kernel<<<b2, 256, 0, st>>>(Q, D, Sm, n, p, out);
   return cudaGetLastError();
 }
 
@@ -162,8 +290,8 @@ cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64
   const dim3 grid((unsigned)((n2 + BN - 1) / BN), (unsigned)((n1 + BM - 1) / BM),
                   (unsigned)p);
   count_launch(1);
-  gemm_tile_kernel<<<grid, NT, 0, st>>>(A, m, 1, n1 * m, B, m * n2, C, n1 * n2, n1, m, n2,
-                                        nullptr, nullptr, nullptr, nullptr);
+  gemm_tile_kernel<<<grid, NT, 0, st>>>(A, m, 1, n1 * m, B, m * n2, n2, 1, C, n1 * n2, n1, m,
+                                        n2, nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

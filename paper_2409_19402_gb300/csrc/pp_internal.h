@@ -46,9 +46,20 @@ int64_t mode3_tc_partials(int64_t P, int64_t N);
 // Batched FP32 GEMM Y[z] (P x N) = M[z] (P x S) * X[z] (S x N), M(r, c) =
 // Mm[z*sMz + r*sr + c*sc], X and Y row-major with leading dimension N; a batch
 // stride of 0 broadcasts an operand over the batch.
+// X may be strided: X(c, n) = X[z*sXz + c*sxc + n*sxn] (sxc < 0: row-major, sxc = N).
 cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
                                 const float *X, int64_t sXz, float *Y, int64_t sYz, int64_t P,
-                                int64_t S, int64_t N, int64_t batch, cudaStream_t st);
+                                int64_t S, int64_t N, int64_t batch, cudaStream_t st,
+                                int64_t sxc = -1, int64_t sxn = 1);
+
+// out (R x S) = [out +] A B^T for A (R x K), B (S x K) row-major, split over K into
+// nt_splits(R, S, K) FP32 partials (part) summed in a fixed order.
+int64_t nt_splits(int64_t R, int64_t S, int64_t K);
+cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
+                                 float *part, float *out, int accumulate, cudaStream_t st);
+// out = D - Q sym(Q^T D) for Q, D n x p (Sm: p x p scratch)
+cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p, float *Sm,
+                           float *out, cudaStream_t st);
 
 // Batched facewise product C_t = A_t B_t (Def. 2.3).
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
