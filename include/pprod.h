@@ -77,7 +77,8 @@ typedef enum pp_op {
     PP_OP_TSVDQ = 3,
     PP_OP_TSVDQII = 4,
     PP_OP_HOSVD = 5,
-    PP_OP_PPROD_BWD = 6
+    PP_OP_PPROD_BWD = 6,
+    PP_OP_U3 = 7
 } pp_op;
 
 /* Problem sizes for pp_workspace_bytes.  Fields an op does not use are
@@ -238,6 +239,43 @@ PP_API pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_
                                float *Ak_hosvd, pp_hosvd_report *rep,
                                const pp_opts *opts, void *ws, size_t ws_bytes,
                                void *stream);
+
+/*
+ * Matched-storage HOSVD truncation (Sec. 5.3, the storage equations that fix
+ * the HOSVD rank k2 from the *Q-SVD truncation k).  Returns in *k2 the largest
+ * integer k2 >= 1 whose truncated HOSVD costs no more storage than the
+ * truncated *Q-SVD with truncation k (both with the n x p factor Q / U3):
+ *   variant 0, multirank (l, k2, p):   l k2 p + l^2 + m k2 + n p <= k (l + m) p + n p
+ *   variant 1, multirank (k2, k2, p):  k2^2 p + l k2 + m k2 + n p <= k (l + m) p + n p
+ * i.e. the equations solved for k2 and rounded down, capped at m (variant 0)
+ * or min(l, m) (variant 1).  *k2 = 0 when no k2 >= 1 fits.  Host-only: no
+ * device work.  PP_EINVAL for NULL k2 or another variant; PP_ESHAPE unless
+ * 1 <= p <= n and 1 <= k <= min(l, m).  The *Q-SVDII energy with the same
+ * error bound (Thm. 4.5) is rep.kept2 / rep.normAh2 of the tsvdq_trunc report.
+ */
+PP_API pp_status pp_hosvd_matched_k2(int64_t l, int64_t m, int64_t n, int64_t p, int64_t k,
+                                     int32_t variant, int64_t *k2);
+
+/*
+ * U3 transformation (Thm. 4.3, Cor. 4.1; the data-dependent Q of Sec. 5.1.1).
+ *   A is l x m x n, 1 <= p <= n <= 768.
+ * Q (n x p, row-major) receives the leading p left singular vectors of the
+ * mode-3 unfolding A_(3), computed as eigenvectors of the n x n Gram matrix
+ * A_(3) A_(3)^T (FP32 products over the l*m pixels, split into partial sums
+ * that are added in a fixed order) by the one-sided Jacobi SVD of that
+ * symmetric matrix; columns in descending eigenvalue order, each with the sign
+ * that makes its largest-magnitude entry (the first on ties) positive.
+ * lambda (p, FP32, may be NULL) receives the eigenvalues sigma_j(A_(3))^2.
+ * rep (device, may be NULL): status, sweeps, K = kappa = p, normA2 = trace of
+ * the Gram (|A|_F^2), normAh2 = kept2 = the sum of the p eigenvalues
+ * (|A x_3 Q^T|_F^2 by Cor. 4.1), discarded2 = proj_err2 = normA2 - normAh2
+ * (the projection error of Cor. 4.1; cancellation when it is small), err2 = 0.
+ * opts: max_sweeps, jacobi_tol and check_finite apply.
+ * Workspace: pp_workspace_bytes(PP_OP_U3, {l, m, n, p}).  PP_ENOSYS for n > 768.
+ */
+PP_API pp_status pprod_u3(const float *A, int64_t l, int64_t m, int64_t n, int64_t p, float *Q,
+                          float *lambda, pp_report *rep, const pp_opts *opts, void *ws,
+                          size_t ws_bytes, void *stream);
 
 /*
  * Batched *Q-SVDII over independent tensors of uneven sizes (one item per

@@ -337,6 +337,21 @@ def storage_hosvd(n1: int, n2: int, n3: int, k1: int, k2: int, k3: int) -> int:
     return k1 * k2 * k3 + n1 * k1 + n2 * k2 + n3 * k3
 
 
+def hosvd_matched_k2(n1: int, n2: int, n3: int, p: int, k: int, variant: int) -> int:
+    """Sec. 5.3 storage matching, by exhaustive search: the largest k2 in
+    1..n2 (variant 0, HOSVD multirank (n1, k2, p)) or 1..min(n1, n2) (variant 1,
+    multirank (k2, k2, p)) whose HOSVD storage (U3 = Q counted) does not exceed
+    the *Q-SVD storage with truncation k plus the n3 p of Q; 0 if none does."""
+    budget = storage_tsvdq(n1, n2, k, p) + n3 * p
+    best = 0
+    top = n2 if variant == 0 else min(n1, n2)
+    for k2 in range(1, top + 1):
+        k1 = n1 if variant == 0 else k2
+        if storage_hosvd(n1, n2, n3, k1, k2, p) <= budget:
+            best = k2
+    return best
+
+
 def compression_ratio(n1: int, n2: int, n3: int, st_approx: int, st_q: int) -> float:
     """CR = st[A] / (st[A~] + st[Q]) with st[A] = n1 n2 n3 (Sec. 5.1.2)."""
     return float(n1 * n2 * n3) / float(st_approx + st_q)

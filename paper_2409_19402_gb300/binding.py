@@ -24,6 +24,7 @@ PP_OK, PP_EINVAL, PP_ESHAPE, PP_ENOTORTHO, PP_ENONFINITE, PP_ENOCONV = 0, 1, 2, 
 PP_ETIMEOUT, PP_EWORKSPACE, PP_ECUDA, PP_ENOSYS = 6, 7, 8, 9
 PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII, PP_OP_HOSVD = 0, 1, 2, 3, 4, 5
 PP_OP_PPROD_BWD = 6
+PP_OP_U3 = 7
 
 
 class PPError(RuntimeError):
@@ -104,6 +105,11 @@ def lib() -> ctypes.CDLL:
         L.tsvdqII_noalloc.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp,
                                       vp, vp, vp, vp, ctypes.POINTER(pp_opts), vp]
         L.tsvdqII_noalloc.restype = i32
+        L.pprod_u3.argtypes = [vp, i64, i64, i64, i64, vp, vp, vp, ctypes.POINTER(pp_opts), vp,
+                               sz, vp]
+        L.pprod_u3.restype = i32
+        L.pp_hosvd_matched_k2.argtypes = [i64, i64, i64, i64, i64, i32, ctypes.POINTER(i64)]
+        L.pp_hosvd_matched_k2.restype = i32
         L.pp_set_jacobi_shape.argtypes = [i64, i64, i64, i32, i32]
         L.pp_set_jacobi_shape.restype = i32
         L.pp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
@@ -373,6 +379,35 @@ def hosvd_compare(A: torch.Tensor, Q: torch.Tensor, k1: int, k2: int, want_ak: b
                                0 if ws is None else ws.numel(), _stream(stream)), "hosvd_compare")
     raw = bytes(rep.cpu().numpy().tobytes())
     return pp_hosvd_report.from_buffer_copy(raw), Ak
+
+
+def pprod_u3(A: torch.Tensor, p: int, ws=None, stream=None, **opts):
+    """U3 transformation (Thm. 4.3): Q (n, p) = leading eigenvectors of A_(3) A_(3)^T,
+    lambda (p) their eigenvalues, and the device pp_report (uint8 tensor; read_report)."""
+    _check_t(A, "A")
+    n, l, m = A.shape
+    dev = A.device
+    Q = torch.empty((n, p), dtype=torch.float32, device=dev)
+    lam = torch.empty((p,), dtype=torch.float32, device=dev)
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_U3, l=l, m=m, n=n, p=p)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().pprod_u3(_ptr(A), l, m, n, int(p), _ptr(Q), _ptr(lam), _ptr(rep),
+                          ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(),
+                          _stream(stream)), "pprod_u3")
+    return Q, lam, rep
+
+
+def hosvd_matched_k2(l: int, m: int, n: int, p: int, k: int, variant: int) -> int:
+    """Sec. 5.3 storage matching: largest HOSVD rank k2 with multirank (l, k2, p)
+    (variant 0) or (k2, k2, p) (variant 1) storing no more than the *Q-SVD with
+    truncation k; 0 when none fits.  Host-only."""
+    out = ctypes.c_int64(0)
+    _raise(lib().pp_hosvd_matched_k2(int(l), int(m), int(n), int(p), int(k), int(variant),
+                                     ctypes.byref(out)), "pp_hosvd_matched_k2")
+    return int(out.value)
 
 
 class Batch:

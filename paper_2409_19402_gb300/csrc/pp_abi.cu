@@ -2,6 +2,7 @@
 // argument validation, workspace carving and the stream-ordered launch
 // sequence of each operation.  No entry point allocates, frees, copies to or
 // from the host, or synchronises.
+#include <math.h>
 #include <string.h>
 
 #include <algorithm>
@@ -138,6 +139,26 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
   w.part = c.take<float>(z * n * p);
   w.dQE = c.take<float>(n * p);
   w.Sm = c.take<float>(p * p);
+  return w;
+}
+
+struct U3Ws {
+  float *part, *G, *W, *sig, *Uh, *s, *Vh;
+  int32_t *perm, *sweeps, *status;
+};
+
+U3Ws carve_u3(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p) {
+  U3Ws w;
+  w.part = c.take<float>(pp::nt_splits(n, n, l * m) * n * n);
+  w.G = c.take<float>(n * n);
+  w.W = c.take<float>(n * pp::jacobi_apad(n, n));
+  w.sig = c.take<float>(n);
+  w.Uh = c.take<float>(n * p);
+  w.s = c.take<float>(p);
+  w.Vh = c.take<float>(n * p);
+  w.perm = c.take<int32_t>(n);
+  w.sweeps = c.take<int32_t>(1);
+  w.status = c.take<int32_t>(1);
   return w;
 }
 
@@ -316,6 +337,10 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
           bad_dims(sh->l, sh->n2, sh->n, sh->p))
         return 0;
       carve_bwd(c, sh->l, sh->m, sh->n2, sh->n, sh->p);
+      return c.off;
+    case PP_OP_U3:
+      if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
+      carve_u3(c, sh->l, sh->m, sh->n, sh->p);
       return c.off;
     case PP_OP_HOSVD:
       if (bad_dims(sh->l, sh->m, sh->n, sh->p) || sh->k < 1 || sh->k > sh->l || sh->n2 < 1 ||
@@ -698,6 +723,91 @@ pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m, in
     ra.err2_hosvd = w.scal + 3;
     PP_TRY(pp::launch_hosvd_report(ra, st));
   }
+  return PP_OK;
+}
+
+pp_status pprod_u3(const float *A, int64_t l, int64_t m, int64_t n, int64_t p, float *Q,
+                   float *lambda, pp_report *rep, const pp_opts *opts, void *ws, size_t ws_bytes,
+                   void *stream) {
+  if (!A || !Q) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  if (n > MAX_LONG_SIDE) return PP_ENOSYS;
+  pp_shape sh{l, m, n, p, 0, 0};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_U3, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const U3Ws w = carve_u3(c, l, m, n, p);
+  PP_TRY(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+  if (o.check_finite) PP_TRY(pp::launch_check_finite(A, n * l * m, w.status, st));
+  // Gram of the mode-3 unfolding: G = A_(3) A_(3)^T, A_(3) is n x (l m) row-major
+  PP_TRY(pp::launch_nt_accumulate(A, A, n, n, l * m, w.part, w.G, 0, st));
+  // its eigenvectors: one-sided Jacobi SVD of the symmetric PSD G (one n x n slice)
+  pp::JacobiArgs ja;
+  ja.X = w.G;
+  ja.W = w.W;
+  ja.sig = w.sig;
+  ja.perm = w.perm;
+  ja.sweeps = w.sweeps;
+  ja.status = w.status;
+  ja.l = n;
+  ja.m = n;
+  ja.p = 1;
+  ja.max_sweeps = o.max_sweeps;
+  ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(n, n);
+  PP_TRY(pp::launch_jacobi(ja, st));
+  // leading p: the long-side (normalised rotated) vectors, orthonormal to working accuracy
+  pp::FactorArgs fa;
+  fa.X = w.G;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = n;
+  fa.m = n;
+  fa.p = 1;
+  fa.b = n;
+  fa.a_pad = pp::jacobi_apad(n, n);
+  fa.kfix = p;
+  fa.rho = nullptr;
+  fa.offs = nullptr;
+  fa.Uh = w.Uh;
+  fa.s = w.s;
+  fa.Vh = w.Vh;
+  fa.Ahk = nullptr;
+  fa.kept_partial = nullptr;
+  fa.disc_partial = nullptr;
+  PP_TRY(pp::launch_factors(fa, st));
+  PP_TRY(pp::launch_u3_finish(w.Vh, w.s, w.G, n, p, Q, lambda, w.status, w.sweeps, rep, st));
+  return PP_OK;
+}
+
+pp_status pp_hosvd_matched_k2(int64_t l, int64_t m, int64_t n, int64_t p, int64_t k,
+                              int32_t variant, int64_t *k2) {
+  if (!k2 || (variant != 0 && variant != 1)) return PP_EINVAL;
+  *k2 = 0;
+  if (l < 1 || m < 1 || n < 1 || p < 1 || p > n || k < 1 || k > (l < m ? l : m) ||
+      l > (1 << 20) || m > (1 << 20) || n > (1 << 20))
+    return PP_ESHAPE;
+  // budget: *Q-SVD storage k (l + m) p (Sec. 5.1.2); the n p of Q is on both sides
+  const int64_t budget = k * (l + m) * p;
+  int64_t r;
+  if (variant == 0) {
+    // HOSVD(l, k2, p): l k2 p + l^2 + m k2 <= budget, linear in k2
+    const int64_t num = budget - l * l, den = l * p + m;
+    r = num < 0 ? 0 : num / den;
+    if (r > m) r = m;
+  } else {
+    // HOSVD(k2, k2, p): p k2^2 + (l + m) k2 <= budget; the positive root, then
+    // corrected in integers so that r is the largest k2 that fits
+    const double b = (double)(l + m), pd = (double)p;
+    r = (int64_t)((-b + sqrt(b * b + 4.0 * pd * (double)budget)) / (2.0 * pd));
+    auto cost = [&](int64_t x) { return p * x * x + (l + m) * x; };
+    while (r > 0 && cost(r) > budget) --r;
+    while (cost(r + 1) <= budget) ++r;
+    const int64_t cap = l < m ? l : m;
+    if (r > cap) r = cap;
+  }
+  *k2 = r < 1 ? 0 : r;
   return PP_OK;
 }
 

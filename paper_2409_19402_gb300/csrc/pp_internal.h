@@ -134,6 +134,13 @@ cudaError_t launch_gram(const float *A, int64_t l, int64_t m, int64_t n, int mod
 // P (d x d) = U U^T for U d x k row-major.
 cudaError_t launch_projector(const float *U, int64_t d, int64_t k, float *P, cudaStream_t st);
 
+// U3 builder epilogue (n <= 768): Q (n x p) = V, trailing zero columns (zero
+// eigenvalues) completed to an orthonormal basis, each column's largest-magnitude
+// entry made positive, lambda (p, may be null) = s, rep (may be null) from the Gram's
+// trace and the kept eigenvalues (Cor. 4.1).
+cudaError_t launch_u3_finish(const float *V, const float *s, const float *G, int64_t n, int64_t p,
+                             float *Q, float *lambda, int32_t *status, const int32_t *sweeps,
+                             pp_report *rep, cudaStream_t st);
 struct HosvdReportArgs {
   pp_hosvd_report *rep;
   const int32_t *status;

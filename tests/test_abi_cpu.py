@@ -119,3 +119,38 @@ def test_autotune_candidates():
     assert (1, 16) in c and (5, 16) in c and (8, 32) in c
     assert all(C == 1 or 120 >= 4 * C for C, _ in c)
     assert autotune.candidates(6, 9) == [(1, 16)]
+
+
+def test_matched_storage_k2_matches_the_oracle_search():
+    """pp_hosvd_matched_k2 (closed form, host) equals the oracle's exhaustive
+    search over k2 on a grid of shapes, including the infeasible cases."""
+    import numpy as np
+    import oracle
+    b = _lib()
+    rng = np.random.default_rng(12)
+    cases = [(512, 512, 224, 50, 20), (120, 160, 300, 50, 5), (512, 512, 224, 1, 1),
+             (32, 24, 16, 4, 3), (7, 5, 3, 3, 5)]
+    for _ in range(300):
+        n1, n2 = (int(x) for x in rng.integers(2, 400, 2))
+        n3 = int(rng.integers(1, 400))
+        cases.append((n1, n2, n3, int(rng.integers(1, n3 + 1)), int(rng.integers(1, min(n1, n2) + 1))))
+    for (l, m, n, p, k) in cases:
+        for v in (0, 1):
+            assert b.hosvd_matched_k2(l, m, n, p, k, v) == oracle.hosvd_matched_k2(l, m, n, p, k, v), \
+                (l, m, n, p, k, v)
+    L = b.lib()
+    out = ctypes.c_int64(-1)
+    assert L.pp_hosvd_matched_k2(10, 10, 10, 2, 3, 2, ctypes.byref(out)) == b.PP_EINVAL
+    assert L.pp_hosvd_matched_k2(10, 10, 10, 2, 3, 0, None) == b.PP_EINVAL
+    assert L.pp_hosvd_matched_k2(10, 10, 10, 11, 3, 0, ctypes.byref(out)) == b.PP_ESHAPE
+    assert L.pp_hosvd_matched_k2(10, 10, 10, 2, 11, 0, ctypes.byref(out)) == b.PP_ESHAPE
+
+
+def test_u3_builder_host_validation():
+    b = _lib()
+    L = b.lib()
+    assert b.workspace_bytes(b.PP_OP_U3, l=120, m=160, n=300, p=50) > 300 * 300 * 4
+    assert L.pprod_u3(None, 4, 4, 8, 2, FAKE, None, None, None, FAKE, 1 << 30, None) == b.PP_EINVAL
+    assert L.pprod_u3(FAKE, 4, 4, 8, 9, FAKE, None, None, None, FAKE, 1 << 30, None) == b.PP_ESHAPE
+    assert L.pprod_u3(FAKE, 4, 4, 1000, 9, FAKE, None, None, None, FAKE, 1 << 40, None) == b.PP_ENOSYS
+    assert L.pprod_u3(FAKE, 4, 4, 8, 2, FAKE, None, None, None, FAKE, 16, None) == b.PP_EWORKSPACE

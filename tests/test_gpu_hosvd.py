@@ -55,3 +55,35 @@ def test_hosvd_video_shaped():
 def test_hosvd_hyperspectral_shaped_reduced():
     A = inputs.hyperspectral(l=128, m=128, n=224)
     _case(A, 10, 20, 20)
+
+
+def test_section_5_3_comparison_pipeline_on_the_gpu():
+    """The Sec. 5.3 protocol end to end on the device: Q = U3 from pprod_u3, the
+    *Q-SVD with truncation k, the *Q-SVDII energy gamma = kept / |A-hat|^2 taken
+    from that run (no worse, Thm. 4.5), and the HOSVD (k2, k2, p) with k2 from
+    the storage equations (no more storage than the *Q-SVD), whose error matches
+    the oracle's HOSVD at the same k2."""
+    b = _b()
+    A = inputs.hyperspectral(l=128, m=128, n=224)
+    n, l, m = A.shape
+    p, k = 25, 5
+    Ad = torch.from_numpy(A).cuda()
+    Qd, _, _ = b.pprod_u3(Ad, p)
+    tq = b.tsvdq_trunc(Ad, Qd, k)
+    r1 = tq.report()
+    assert r1.status == 0
+    gamma = r1.kept2 / r1.normAh2
+    r2 = b.tsvdqII(Ad, Qd, gamma).report()
+    assert r2.status == 0
+    assert r2.err2 <= r1.err2 * (1 + 1e-5)                           # Thm. 4.5
+    assert oracle.storage_tsvdqII(l, m, r2.kappa) <= oracle.storage_tsvdq(l, m, k, p)
+    k2 = b.hosvd_matched_k2(l, m, n, p, k, 1)
+    assert k2 >= 1
+    assert (oracle.storage_hosvd(l, m, n, k2, k2, p)
+            <= oracle.storage_tsvdq(l, m, k, p) + n * p)
+    rep, _ = b.hosvd_compare(Ad, Qd, k2, k2)
+    assert rep.status == 0
+    Q = Qd.cpu().numpy()
+    _, e_hos = oracle.hosvd(A, k2, k2, Q)
+    nA = float(np.sqrt((A.astype(np.float64) ** 2).sum()))
+    assert abs(np.sqrt(rep.err2_hosvd) - np.sqrt(e_hos)) <= 1e-6 * nA

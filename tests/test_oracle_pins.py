@@ -448,6 +448,38 @@ def test_metrics_storage_formulas():
     assert oracle.compression_ratio(10, 10, 10, 50, 50) == pytest.approx(10.0)
 
 
+def test_matched_storage_k2_worked_values():
+    """Sec. 5.3 storage equations worked by hand for a hyperspectral-sized case
+    (n1 = n2 = 512, n3 = 224, p = 50, k = 20; *Q-SVD budget 20*1024*50 =
+    1,024,000 besides Q):
+      (n1, k2, p):  k2 (512*50 + 512) <= 1,024,000 - 512^2 = 761,856
+                    -> k2 <= 761,856 / 26,112 = 29.18 -> 29
+      (k2, k2, p):  50 k2^2 + 1024 k2 <= 1,024,000: k2 = 133 costs 1,020,642,
+                    k2 = 134 costs 1,035,016 -> 133"""
+    assert oracle.hosvd_matched_k2(512, 512, 224, 50, 20, 0) == 29
+    assert oracle.hosvd_matched_k2(512, 512, 224, 50, 20, 1) == 133
+    # no feasible k2: the full U1 (n1^2) alone exceeds the budget
+    assert oracle.hosvd_matched_k2(512, 512, 224, 1, 1, 0) == 0
+
+
+def test_matched_storage_k2_is_the_rounded_down_root():
+    """The exhaustive search equals the real root of each storage equation,
+    rounded down (the paper's 'solve and round down'), clipped to the range."""
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        n1, n2 = (int(x) for x in rng.integers(4, 300, 2))
+        n3 = int(rng.integers(2, 300))
+        p = int(rng.integers(1, n3 + 1))
+        k = int(rng.integers(1, min(n1, n2) + 1))
+        lhs = k * (n1 + n2) * p
+        r0 = (lhs - n1 * n1) / (n1 * p + n2)
+        b = n1 + n2
+        r1 = (-b + math.sqrt(b * b + 4.0 * p * lhs)) / (2.0 * p)
+        for variant, root, cap in ((0, r0, n2), (1, r1, min(n1, n2))):
+            want = min(cap, math.floor(root + 1e-9)) if root >= 1 else 0
+            assert oracle.hosvd_matched_k2(n1, n2, n3, p, k, variant) == want, (n1, n2, n3, p, k)
+
+
 def test_tiny_config_dct_tsvdq():
     """The tiny config end to end in the oracle: Q = DCT p=4 (Sec. 5.1.1 footnote
     reading), k=3; the error identity holds and sigma match LAPACK per slice."""
