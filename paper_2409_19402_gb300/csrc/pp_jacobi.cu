@@ -291,12 +291,74 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// One pair per group of GW lanes (16 or 32).  na, nb: tracked squared norms in
-// shared memory; lane is the lane index within the group.
+// Sum of v over the GW lanes of this thread's group, bitwise identical in all
+// of them: each lane posts its partial to its warp's 32-float scratch (wred)
+// and reads the group's GW partials back, added in a fixed tree.  One
+// shared-memory round trip is much shorter than log2(GW) dependent shuffles.
+template <int GW>
+__device__ __forceinline__ float group_sum_smem(float v, float *wred, unsigned mask) {
+  const int wl = threadIdx.x & 31;
+  wred[wl] = v;
+  __syncwarp(mask);
+  const float4 *rp = reinterpret_cast<const float4 *>(wred + (wl & ~(GW - 1)));
+  float sv[GW / 4];
+#pragma unroll
+  for (int k = 0; k < GW / 4; ++k) {
+    const float4 q = rp[k];
+    sv[k] = (q.x + q.y) + (q.z + q.w);
+  }
+#pragma unroll
+  for (int w = GW / 8; w > 0; w >>= 1)
+#pragma unroll
+    for (int k = 0; k < w; ++k) sv[k] += sv[k + w];
+  __syncwarp(mask);
+  return sv[0];
+}
+
+// Rotation parameters for a pair with squared norms al, be and inner product g:
+// the Rutishauser form x' = x - s (y + tau x), y' = y + s (x - tau y) of the
+// symmetric Schur rotation that zeroes g; t is its tangent.
+__device__ __forceinline__ void pair_angle(float g, float al, float be, float &t, float &s,
+                                           float &tau) {
+  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (be - al) / (2 g), written
+  // without zeta: t = sign(d) 2g / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
+  const float d = be - al, g2x = 2.f * g;
+  const float r = fmaf(d, d, g2x * g2x);
+  const float h = r * rsqrtf(r);
+  t = copysignf(1.f, d) * __fdividef(g2x, fabsf(d) + h);
+  const float u = fmaf(t, t, 1.f);
+  float c = rsqrtf(u);
+  c = c * fmaf(-0.5f * u * c, c, 1.5f);          // one Newton step: c = 1/sqrt(1 + t^2)
+  s = c * t;
+  // tau = s / (1 + c) (Rutishauser: implied cosine 1 - s tau), reciprocal refined
+  // by one Newton step so that tau is accurate to about half an ulp
+  const float onec = 1.f + c;                    // in [1, 2]: no special cases
+  float rc = __fdividef(1.f, onec);
+  rc = fmaf(rc, fmaf(-onec, rc, 1.f), rc);
+  tau = s * rc;
+}
+
+__device__ __forceinline__ void rotate4(float4 &x, float4 &y, float s, float tau) {
+  float4 nx, ny;
+  nx.x = fmaf(-s, fmaf(tau, x.x, y.x), x.x);
+  ny.x = fmaf(s, fmaf(-tau, y.x, x.x), y.x);
+  nx.y = fmaf(-s, fmaf(tau, x.y, y.y), x.y);
+  ny.y = fmaf(s, fmaf(-tau, y.y, x.y), y.y);
+  nx.z = fmaf(-s, fmaf(tau, x.z, y.z), x.z);
+  ny.z = fmaf(s, fmaf(-tau, y.z, x.z), y.z);
+  nx.w = fmaf(-s, fmaf(tau, x.w, y.w), x.w);
+  ny.w = fmaf(s, fmaf(-tau, y.w, x.w), y.w);
+  x = nx;
+  y = ny;
+}
+
+// One pair per group of GW lanes (8, 16 or 32).  na, nb: tracked squared norms
+// in shared memory; lane is the lane index within the group; wred is the
+// warp's 32-float reduction scratch.
 template <int GW, int CW>
 __device__ __forceinline__ bool jacobi_pair_warp(float *__restrict__ x, float *__restrict__ y,
                                                  float *na, float *nb, int n4, float tol2,
-                                                 int lane, unsigned mask) {
+                                                 int lane, unsigned mask, float *wred) {
   float4 xv[CW], yv[CW];
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
 #pragma unroll
@@ -311,48 +373,63 @@ __device__ __forceinline__ bool jacobi_pair_warp(float *__restrict__ x, float *_
       g3 = fmaf(xv[q].w, yv[q].w, g3);
     }
   }
-  float g = (g0 + g1) + (g2 + g3);
-#pragma unroll
-  for (int off = GW / 2; off > 0; off >>= 1) g += __shfl_xor_sync(mask, g, off, GW);
+  const float g = group_sum_smem<GW>((g0 + g1) + (g2 + g3), wred, mask);
   const float al = *na, be = *nb;
   if (g == 0.f || g * g <= tol2 * al * be) return false;
-  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (be - al) / (2 g), written
-  // without zeta: t = sign(d) 2g / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
-  const float d = be - al, g2x = 2.f * g;
-  const float r = fmaf(d, d, g2x * g2x);
-  const float h = r * rsqrtf(r);
-  const float t = copysignf(1.f, d) * __fdividef(g2x, fabsf(d) + h);
-  const float u = fmaf(t, t, 1.f);
-  float c = rsqrtf(u);
-  c = c * fmaf(-0.5f * u * c, c, 1.5f);          // one Newton step: c = 1/sqrt(1 + t^2)
-  const float s = c * t;
-  // tau = s / (1 + c) (Rutishauser: implied cosine 1 - s tau), reciprocal refined
-  // by one Newton step so that tau is accurate to about half an ulp
-  const float onec = 1.f + c;                    // in [1, 2]: no special cases
-  float rc = __fdividef(1.f, onec);
-  rc = fmaf(rc, fmaf(-onec, rc, 1.f), rc);
-  const float tau = s * rc;
+  float t, s, tau;
+  pair_angle(g, al, be, t, s, tau);
 #pragma unroll
   for (int q = 0; q < CW; ++q) {
     const int e4 = lane + GW * q;
     if (e4 < n4) {
-      float4 nx, ny;
-      nx.x = fmaf(-s, fmaf(tau, xv[q].x, yv[q].x), xv[q].x);
-      ny.x = fmaf(s, fmaf(-tau, yv[q].x, xv[q].x), yv[q].x);
-      nx.y = fmaf(-s, fmaf(tau, xv[q].y, yv[q].y), xv[q].y);
-      ny.y = fmaf(s, fmaf(-tau, yv[q].y, xv[q].y), yv[q].y);
-      nx.z = fmaf(-s, fmaf(tau, xv[q].z, yv[q].z), xv[q].z);
-      ny.z = fmaf(s, fmaf(-tau, yv[q].z, xv[q].z), yv[q].z);
-      nx.w = fmaf(-s, fmaf(tau, xv[q].w, yv[q].w), xv[q].w);
-      ny.w = fmaf(s, fmaf(-tau, yv[q].w, xv[q].w), yv[q].w);
-      reinterpret_cast<float4 *>(x)[e4] = nx;
-      reinterpret_cast<float4 *>(y)[e4] = ny;
+      rotate4(xv[q], yv[q], s, tau);
+      reinterpret_cast<float4 *>(x)[e4] = xv[q];
+      reinterpret_cast<float4 *>(y)[e4] = yv[q];
     }
   }
   if (lane == 0) {
     *na = fmaxf(fmaf(-t, g, al), 0.f);
     *nb = fmaf(t, g, be);
   }
+  return true;
+}
+
+// The same rotation with x held in registers (xv) and its tracked squared norm
+// al in a register of every lane of the group (every lane gets the same g, so
+// every lane updates al identically).
+template <int GW, int CW>
+__device__ __forceinline__ bool jacobi_pair_reg(float4 (&xv)[CW], float &al,
+                                                float *__restrict__ y, float *nb, int n4,
+                                                float tol2, int lane, unsigned mask,
+                                                float *wred) {
+  float4 yv[CW];
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) {
+      yv[q] = reinterpret_cast<const float4 *>(y)[e4];
+      g0 = fmaf(xv[q].x, yv[q].x, g0);
+      g1 = fmaf(xv[q].y, yv[q].y, g1);
+      g2 = fmaf(xv[q].z, yv[q].z, g2);
+      g3 = fmaf(xv[q].w, yv[q].w, g3);
+    }
+  }
+  const float g = group_sum_smem<GW>((g0 + g1) + (g2 + g3), wred, mask);
+  const float be = *nb;
+  if (g == 0.f || g * g <= tol2 * al * be) return false;
+  float t, s, tau;
+  pair_angle(g, al, be, t, s, tau);
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) {
+      rotate4(xv[q], yv[q], s, tau);
+      reinterpret_cast<float4 *>(y)[e4] = yv[q];
+    }
+  }
+  al = fmaxf(fmaf(-t, g, al), 0.f);
+  if (lane == 0) *nb = fmaf(t, g, be);
   return true;
 }
 
@@ -378,7 +455,7 @@ __device__ __forceinline__ unsigned group_mask() {
 
 template <int GW, int CW>
 __device__ int cross_pass_warp(float *top, float *bot, float *ntop, float *nbot, int bs,
-                               int a_pad, float tol2) {
+                               int a_pad, float tol2, float *wred) {
   const int lane = threadIdx.x % GW, warp = threadIdx.x / GW, nw = blockDim.x / GW;
   const unsigned mask = group_mask<GW>();
   const int n4 = a_pad / 4;
@@ -388,7 +465,7 @@ __device__ int cross_pass_warp(float *top, float *bot, float *ntop, float *nbot,
       int j = i + r;
       if (j >= bs) j -= bs;
       if (jacobi_pair_warp<GW, CW>(top + (size_t)i * a_pad, bot + (size_t)j * a_pad, ntop + i,
-                                   nbot + j, n4, tol2, lane, mask) &&
+                                   nbot + j, n4, tol2, lane, mask, wred) &&
           lane == 0)
         ++rot;
     }
@@ -397,9 +474,56 @@ __device__ int cross_pass_warp(float *top, float *bot, float *ntop, float *nbot,
   return rot;
 }
 
+// Cross pass with the top block in registers: group i owns top vector i for
+// all bs rounds (round r pairs it with bottom vector (i + r) mod bs), so only
+// the bottom vectors travel through shared memory; the top vectors and their
+// norms are written back once at the end.  Needs blockDim.x / GW >= bs.  The
+// arithmetic is that of cross_pass_warp, so the results are identical.
+template <int GW, int CW>
+__device__ int cross_pass_reg(float *top, float *bot, float *ntop, float *nbot, int bs,
+                              int a_pad, float tol2, float *wred) {
+  const int lane = threadIdx.x % GW, i = threadIdx.x / GW;
+  const unsigned mask = group_mask<GW>();
+  const int n4 = a_pad / 4;
+  const bool act = i < bs;
+  float4 xv[CW];
+  float al = 0.f;
+  float4 *xt = reinterpret_cast<float4 *>(top + (size_t)(act ? i : 0) * a_pad);
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      const int e4 = lane + GW * q;
+      if (e4 < n4) xv[q] = xt[e4];
+    }
+    al = ntop[i];
+  }
+  int rot = 0;
+  for (int r = 0; r < bs; ++r) {
+    if (act) {
+      int j = i + r;
+      if (j >= bs) j -= bs;
+      if (jacobi_pair_reg<GW, CW>(xv, al, bot + (size_t)j * a_pad, nbot + j, n4, tol2, lane,
+                                  mask, wred) &&
+          lane == 0)
+        ++rot;
+    }
+    __syncthreads();
+  }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < CW; ++q) {
+      const int e4 = lane + GW * q;
+      if (e4 < n4) xt[e4] = xv[q];
+    }
+    if (lane == 0) ntop[i] = al;
+  }
+  __syncthreads();
+  return rot;
+}
+
 template <int GW, int CW>
 __device__ int intra_pass_warp(float *top, float *bot, float *ntop, float *nbot, int bs,
-                               int a_pad, float tol2) {
+                               int a_pad, float tol2, float *wred) {
   const int lane = threadIdx.x % GW, warp = threadIdx.x / GW, nw = blockDim.x / GW;
   const unsigned mask = group_mask<GW>();
   const int n4 = a_pad / 4;
@@ -414,7 +538,7 @@ __device__ int intra_pass_warp(float *top, float *bot, float *ntop, float *nbot,
       circle_pair(N, r, upper ? slot : slot - half, j, k);
       if (j >= bs || k >= bs) continue;
       if (jacobi_pair_warp<GW, CW>(base + (size_t)j * a_pad, base + (size_t)k * a_pad, nb + j,
-                                   nb + k, n4, tol2, lane, mask) &&
+                                   nb + k, n4, tol2, lane, mask, wred) &&
           lane == 0)
         ++rot;
     }
@@ -428,12 +552,25 @@ __host__ __device__ constexpr int clu_max_threads(int gw, int cw) {
   return (gw * cw <= 64 && gw >= 32) ? 1024 : 512;
 }
 
-template <int GW, int CW>
-__global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_kernel(JacobiArgs A, int a_pad,
+// REG variants hold each group's top vector in registers across the cross pass
+// (cross_pass_reg).  They exist for the shapes whose registers allow it without
+// spills (-Xptxas -v): GW = 16 within the 512-thread bound, GW = 8 with a
+// 256-thread bound (up to 255 registers, so fewer CTAs per SM).
+__host__ __device__ constexpr bool clu_has_reg(int gw, int cw) {
+  return (gw == 16 && cw <= 3) || (gw == 8 && cw <= 8);
+}
+__host__ __device__ constexpr int clu_bound(int gw, int cw, bool reg) {
+  return (reg && gw == 8) ? 256 : clu_max_threads(gw, cw);
+}
+
+template <int GW, int CW, bool REG>
+__global__ void __launch_bounds__(clu_bound(GW, CW, REG), 1) jacobi_cluster_kernel(JacobiArgs A, int a_pad,
                                                                             int C, int bs) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int blk[2][2];        // block id held in [buffer][top/bottom]
   __shared__ int rot_total;
+  __shared__ __align__(16) float red_scratch[clu_bound(GW, CW, REG)];   // 32 floats per warp
+  float *wred = red_scratch + (threadIdx.x & ~31);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int64_t f = blockIdx.x / C;
@@ -486,9 +623,12 @@ __global__ void __launch_bounds__(clu_max_threads(GW, CW), 1) jacobi_cluster_ker
         block_norms(top, ntop, bs, n4);
         block_norms(bot, nbot, bs, n4);
         __syncthreads();
-        rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+        rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
       }
-      rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2);
+      if (REG && (int)(blockDim.x / GW) >= bs)
+        rot += cross_pass_reg<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+      else
+        rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
       // move the two blocks one seat along the circle (DSMEM copies)
       const int nxt = cur ^ 1;
 #pragma unroll
@@ -559,22 +699,24 @@ size_t cluster_smem(int bs, int a_pad, int64_t b) {
 // One cluster configuration: C CTAs per slice, GW lanes per pair, CW float4 per lane.
 struct ClusterCfg {
   int C = 0, bs = 0, GW = 0, CW = 0, threads = 0;
+  bool reg = false;        // REG variant (top vectors in registers)
   size_t smem = 0;
   int max_clusters = 0;   // co-resident clusters of this shape on the device
 };
 
-template <int GW, int CW>
+template <int GW, int CW, bool REG>
 cudaError_t cluster_cfg_query(const JacobiArgs &A, int a_pad, int C, ClusterCfg &cc) {
   const int64_t b = A.l < A.m ? A.l : A.m;
   cc.C = C;
   cc.bs = (int)((b + 2 * C - 1) / (2 * C));
   cc.GW = GW;
   cc.CW = CW;
+  cc.reg = REG;
   int threads = GW * cc.bs;
-  if (threads > clu_max_threads(GW, CW)) threads = clu_max_threads(GW, CW);
+  if (threads > clu_bound(GW, CW, REG)) threads = clu_bound(GW, CW, REG);
   cc.threads = (int)round_up(threads < 64 ? 64 : threads, 32);
   cc.smem = cluster_smem(cc.bs, a_pad, b);
-  cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<GW, CW>,
+  cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<GW, CW, REG>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc.smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -588,10 +730,10 @@ cudaError_t cluster_cfg_query(const JacobiArgs &A, int a_pad, int C, ClusterCfg 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaOccupancyMaxActiveClusters(&cc.max_clusters, jacobi_cluster_kernel<GW, CW>, &cfg);
+  return cudaOccupancyMaxActiveClusters(&cc.max_clusters, jacobi_cluster_kernel<GW, CW, REG>, &cfg);
 }
 
-template <int GW, int CW>
+template <int GW, int CW, bool REG>
 cudaError_t cluster_launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc,
                            cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
@@ -607,46 +749,78 @@ cudaError_t cluster_launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc,
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   count_launch(1);
-  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<GW, CW>, A, a_pad, cc.C, cc.bs);
+  return cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<GW, CW, REG>, A, a_pad, cc.C, cc.bs);
+}
+
+// Estimated cost of a launch shape: waves x (pair rounds + cluster barriers, each
+// barrier counted as two rounds) per sweep, where a sweep has 2 C bs - 1 pair
+// rounds (bs = ceil(b / 2C): padding vectors cost rounds), the round time grows
+// with the group's reduction depth log2(GW), and a REG round (top vectors in
+// registers) costs about three quarters of a plain one (measured per round).
+double shape_cost(const JacobiArgs &A, const ClusterCfg &cc) {
+  const double waves = (double)((A.p + cc.max_clusters - 1) / cc.max_clusters);
+  const double depth = cc.GW == 8 ? 3.0 : (cc.GW == 16 ? 4.0 : 5.0);
+  return waves * (2.0 * cc.C * cc.bs - 1.0 + 2.0 * (2 * cc.C + 1)) * (1.0 + 0.15 * depth) *
+         (cc.reg ? 0.75 : 1.0);
+}
+
+// One (GW, CW) shape: the cheaper of the plain and (where it exists) the REG variant.
+template <int GW, int CW>
+cudaError_t query_shape(const JacobiArgs &A, int a_pad, int C, ClusterCfg &cc) {
+  cudaError_t e = cluster_cfg_query<GW, CW, false>(A, a_pad, C, cc);
+  if (e != cudaSuccess) return e;
+  if constexpr (clu_has_reg(GW, CW)) {
+    ClusterCfg r;
+    if (cluster_cfg_query<GW, CW, true>(A, a_pad, C, r) == cudaSuccess && r.max_clusters >= 1 &&
+        r.threads >= GW * r.bs &&
+        (cc.max_clusters < 1 || shape_cost(A, r) < shape_cost(A, cc)))
+      cc = r;
+    cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+template <int GW, int CW>
+cudaError_t launch_shape(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStream_t st) {
+  if constexpr (clu_has_reg(GW, CW)) {
+    if (cc.reg) return cluster_launch<GW, CW, true>(A, a_pad, cc, st);
+  }
+  return cluster_launch<GW, CW, false>(A, a_pad, cc, st);
 }
 
 cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc) {
   const int n4 = a_pad / 4;
   if (GW == 8) {
-    if (n4 <= 40) return cluster_cfg_query<8, 5>(A, a_pad, C, cc);
-    return cluster_cfg_query<8, 8>(A, a_pad, C, cc);
+    if (n4 <= 40) return query_shape<8, 5>(A, a_pad, C, cc);
+    return query_shape<8, 8>(A, a_pad, C, cc);
   }
   if (GW == 16) {
-    if (n4 <= 48) return cluster_cfg_query<16, 3>(A, a_pad, C, cc);
-    if (n4 <= 64) return cluster_cfg_query<16, 4>(A, a_pad, C, cc);
-    return cluster_cfg_query<16, 8>(A, a_pad, C, cc);
+    if (n4 <= 48) return query_shape<16, 3>(A, a_pad, C, cc);
+    if (n4 <= 64) return query_shape<16, 4>(A, a_pad, C, cc);
+    return query_shape<16, 8>(A, a_pad, C, cc);
   }
-  if (n4 <= 64) return cluster_cfg_query<32, 2>(A, a_pad, C, cc);
-  if (n4 <= 128) return cluster_cfg_query<32, 4>(A, a_pad, C, cc);
-  return cluster_cfg_query<32, 6>(A, a_pad, C, cc);
+  if (n4 <= 64) return query_shape<32, 2>(A, a_pad, C, cc);
+  if (n4 <= 128) return query_shape<32, 4>(A, a_pad, C, cc);
+  return query_shape<32, 6>(A, a_pad, C, cc);
 }
 
 cudaError_t launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStream_t st) {
   if (cc.GW == 8) {
-    if (cc.CW == 5) return cluster_launch<8, 5>(A, a_pad, cc, st);
-    return cluster_launch<8, 8>(A, a_pad, cc, st);
+    if (cc.CW == 5) return launch_shape<8, 5>(A, a_pad, cc, st);
+    return launch_shape<8, 8>(A, a_pad, cc, st);
   }
   if (cc.GW == 16) {
-    if (cc.CW == 3) return cluster_launch<16, 3>(A, a_pad, cc, st);
-    if (cc.CW == 4) return cluster_launch<16, 4>(A, a_pad, cc, st);
-    return cluster_launch<16, 8>(A, a_pad, cc, st);
+    if (cc.CW == 3) return launch_shape<16, 3>(A, a_pad, cc, st);
+    if (cc.CW == 4) return launch_shape<16, 4>(A, a_pad, cc, st);
+    return launch_shape<16, 8>(A, a_pad, cc, st);
   }
-  if (cc.CW == 2) return cluster_launch<32, 2>(A, a_pad, cc, st);
-  if (cc.CW == 4) return cluster_launch<32, 4>(A, a_pad, cc, st);
-  return cluster_launch<32, 6>(A, a_pad, cc, st);
+  if (cc.CW == 2) return launch_shape<32, 2>(A, a_pad, cc, st);
+  if (cc.CW == 4) return launch_shape<32, 4>(A, a_pad, cc, st);
+  return launch_shape<32, 6>(A, a_pad, cc, st);
 }
 
 // Pick the cluster shape: among C in [2, 8] and GW in {8, 16, 32} whose shared
-// memory fits, minimise waves x (rounds + barrier cost) per sweep, where a sweep
-// has 2 C bs - 1 pair rounds (bs = ceil(b / 2C): padding vectors cost rounds)
-// and 2C + 1 cluster barriers (each counted as two rounds), and the round time
-// grows with the group's reduction depth log2(GW).  Returns false when no
-// shape applies.
+// memory fits, minimise shape_cost.  Returns false when no shape applies.
 bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
   const int64_t b = A.l < A.m ? A.l : A.m;
   double best_cost = 1e300;
@@ -668,9 +842,7 @@ bool pick_cluster(const JacobiArgs &A, int a_pad, ClusterCfg &best) {
         cudaGetLastError();
         continue;
       }
-      const double waves = (double)((A.p + cc.max_clusters - 1) / cc.max_clusters);
-      const double depth = GW == 8 ? 3.0 : (GW == 16 ? 4.0 : 5.0);
-      const double cost = waves * (2.0 * C * bs - 1.0 + 2.0 * (2 * C + 1)) * (1.0 + 0.15 * depth);
+      const double cost = shape_cost(A, cc);
       if (cost < best_cost * (1.0 - 1e-9)) {
         best_cost = cost;
         best = cc;
@@ -721,8 +893,8 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
         (int64_t)cluster_smem(bs, a_pad, b) <= SMEM_BUDGET &&
         query(A, a_pad, regC, regG, cc) == cudaSuccess && cc.max_clusters >= 1) {
       if (log)
-        fprintf(stderr, "[pprod] jacobi cluster (registered): p=%lld C=%d bs=%d GW=%d\n",
-                (long long)A.p, cc.C, cc.bs, cc.GW);
+        fprintf(stderr, "[pprod] jacobi cluster (registered): p=%lld C=%d bs=%d GW=%d reg=%d\n",
+                (long long)A.p, cc.C, cc.bs, cc.GW, (int)cc.reg);
       return launch(A, a_pad, cc, st);
     }
     cudaGetLastError();
@@ -731,9 +903,10 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
     ClusterCfg cc;
     if (pick_cluster(A, a_pad, cc)) {
       if (log)
-        fprintf(stderr, "[pprod] jacobi cluster: p=%lld C=%d bs=%d GW=%d CW=%d threads=%d "
+        fprintf(stderr, "[pprod] jacobi cluster: p=%lld C=%d bs=%d GW=%d CW=%d reg=%d threads=%d "
                         "smem=%zu max_clusters=%d\n",
-                (long long)A.p, cc.C, cc.bs, cc.GW, cc.CW, cc.threads, cc.smem, cc.max_clusters);
+                (long long)A.p, cc.C, cc.bs, cc.GW, cc.CW, (int)cc.reg, cc.threads, cc.smem,
+                cc.max_clusters);
       return launch(A, a_pad, cc, st);
     }
   }
