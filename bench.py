@@ -188,7 +188,7 @@ def run_reference(args):
 class Runner:
     """Preallocated buffers and a direct C-ABI call for one tsvdqII configuration."""
 
-    def __init__(self, A_dev, Q_dev, gamma, torch, binding):
+    def __init__(self, A_dev, Q_dev, gamma, torch, binding, precond=True):
         import ctypes
         self.t, self.b, self.ct = torch, binding, ctypes
         self.A, self.Q, self.gamma = A_dev, Q_dev, gamma
@@ -207,6 +207,7 @@ class Runner:
         nb = binding.workspace_bytes(binding.PP_OP_TSVDQII, l=l, m=m, n=n, p=p)
         self.ws = torch.empty(nb, dtype=torch.uint8, device=d)
         self.opts = binding.pp_opts()
+        self.opts.precond = 0 if precond else -1
 
     def __call__(self, stream):
         P_ = lambda x: self.ct.c_void_p(x.data_ptr())
@@ -280,7 +281,7 @@ def run_ours(args):
     from paper_2409_19402_gb300 import autotune
     tuned = autotune.tune_jacobi(A_d, Qp_d, gamma=GAMMA, use_cache=False)
     tuned_n = autotune.tune_jacobi(A_d, Qn_d, gamma=GAMMA, use_cache=False) if not args.no_pn else None
-    run = Runner(A_d, Qp_d, GAMMA, torch, binding)
+    run = Runner(A_d, Qp_d, GAMMA, torch, binding, precond=tuned[3])
 
     # stage events: created by recording once, then registered with the library
     stage_events = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -358,12 +359,12 @@ def run_ours(args):
         Kp = int(np.searchsorted(c, need, side="left")) + 1
         Kp = min(max(Kp, 1), len(c))
         gamma_pn = min(1.0, c[Kp - 1] / total)
-        run_pn = Runner(A_d, Qn_d, gamma_pn, torch, binding)
+        run_pn = Runner(A_d, Qn_d, gamma_pn, torch, binding, precond=tuned_n[3])
         t_pn, _ = timed_steps(run_pn, args.steps, args.warmup, torch, flush, stream)
         rpn = run_pn.report()
         ms_pn = sum(t_pn) / args.steps
         pn = {"p": N, "gamma": gamma_pn, "ms_per_step": ms_pn,
-              "jacobi_shape": {"C": tuned_n[0], "GW": tuned_n[1]},
+              "jacobi_shape": {"C": tuned_n[0], "GW": tuned_n[1], "qr_precond": tuned_n[3]},
               "value": L * M * N / (ms_pn / 1e3), "err2": rpn.err2, "err2_target": err_target,
               "kappa": int(rpn.kappa), "speedup_p_lt_n": ms_pn / ms_per_step}
 
@@ -527,7 +528,7 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
                        "parallelism": f"replicas x{world}" if world > 1 else "single",
                        "l2": "flushed before every step (256 MiB write), outside the events",
                        "K": int(rep.K), "kappa": int(rep.kappa), "sweeps": int(rep.sweeps),
-                       "jacobi_shape": {"C": tuned[0], "GW": tuned[1]},
+                       "jacobi_shape": {"C": tuned[0], "GW": tuned[1], "qr_precond": tuned[3]},
                        "RE": math.sqrt(rep.err2 / rep.normA2)},
             "roofline": roofline,
             "stages": stages,

@@ -95,7 +95,9 @@ typedef struct pp_opts {
     float q_tol;          /* orthonormality tolerance (default 1e-5)                */
     int32_t check_finite; /* nonzero: device scan of A for NaN/Inf (default 0)      */
     float jacobi_tol;     /* rotation threshold on |cos| (0 = sqrt(len) * 2^-24)    */
-    int32_t reserved[4];
+    int32_t precond;      /* QR preconditioning of the facewise Jacobi SVD: >= 0 on  */
+                          /* where the slice fits its kernel (default), < 0 off     */
+    int32_t reserved[3];
 } pp_opts;
 
 /* Device-written report of a decomposition call.  Energies are FP64 sums of

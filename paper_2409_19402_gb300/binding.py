@@ -40,7 +40,8 @@ class pp_shape(ctypes.Structure):
 class pp_opts(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int32), ("check_q", ctypes.c_int32),
                 ("q_tol", ctypes.c_float), ("check_finite", ctypes.c_int32),
-                ("jacobi_tol", ctypes.c_float), ("reserved", ctypes.c_int32 * 4)]
+                ("jacobi_tol", ctypes.c_float), ("precond", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class pp_report(ctypes.Structure):
@@ -171,9 +172,10 @@ def _raise(st: int, what: str):
         raise PPError(st, what)
 
 
-def _opts(max_sweeps=0, check_q=False, q_tol=0.0, check_finite=False, jacobi_tol=0.0):
+def _opts(max_sweeps=0, check_q=False, q_tol=0.0, check_finite=False, jacobi_tol=0.0,
+          precond=True):
     return pp_opts(int(max_sweeps), int(bool(check_q)), float(q_tol), int(bool(check_finite)),
-                   float(jacobi_tol))
+                   float(jacobi_tol), 0 if precond else -1)
 
 
 def workspace(nbytes: int, device) -> torch.Tensor | None:

@@ -22,7 +22,7 @@ LIB = os.path.join(LIBDIR, "libpprod.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
-              "--expt-relaxed-constexpr",
+              "--expt-relaxed-constexpr", "-Werror", "all-warnings",
               "-I", os.path.join(ROOT, "include")]
 
 

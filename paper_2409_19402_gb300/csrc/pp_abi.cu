@@ -53,14 +53,25 @@ struct DecompWs {
   int32_t *perm, *sweeps, *status, *rank;
   double *kept_p, *disc_p, *part_a, *part_h, *part_e, *scal, *keys;
   int64_t *K;
+  // QR preconditioner of the Jacobi SVD (slices that fit its shared memory)
+  bool pc;
+  float *R;            // p * b * b
+  int32_t *qperm;      // p * b
+  int64_t wpad;        // row stride of W: jacobi_apad(b, b) with pc, else jacobi_apad(l, m)
 };
 
-DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool ragged) {
+// The workspace always has room for the QR preconditioner where the slice fits
+// its kernel; want_pc (pp_opts.precond >= 0) decides whether it runs.
+DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool ragged,
+                      bool want_pc = true) {
   const int64_t b = l < m ? l : m;
-  const int64_t a_pad = pp::jacobi_apad(l, m);
+  const int64_t a_pad = pp::jacobi_apad(l, m), b_pad = pp::jacobi_apad(b, b);
   DecompWs w{};
+  const bool fits = pp::qrcp_fits(l, m);
+  w.pc = fits && want_pc;
+  w.wpad = w.pc ? b_pad : a_pad;
   w.Ah = c.take<float>(p * l * m);
-  w.W = c.take<float>(p * b * a_pad);
+  w.W = c.take<float>(p * b * (a_pad > b_pad ? a_pad : b_pad));
   w.sig = c.take<float>(p * b);
   w.perm = c.take<int32_t>(p * b);
   w.sweeps = c.take<int32_t>(p);
@@ -77,7 +88,27 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
     w.keys = c.take<double>(p * b);
     w.rank = c.take<int32_t>(p * b);
   }
+  if (fits) {
+    w.R = c.take<float>(p * b * b);
+    w.qperm = c.take<int32_t>(p * b);
+  }
   return w;
+}
+
+// Factor arguments for the Jacobi output of project_and_svd
+pp::FactorArgs decomp_factor_args(const DecompWs &w, int64_t l, int64_t m, int64_t p) {
+  pp::FactorArgs fa{};
+  fa.X = w.Ah;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = l;
+  fa.m = m;
+  fa.p = p;
+  fa.b = l < m ? l : m;
+  fa.a_pad = w.wpad;
+  fa.qperm = w.pc ? w.qperm : nullptr;
+  return fa;
 }
 
 struct HosvdWs {
@@ -91,9 +122,9 @@ struct HosvdWs {
 };
 
 HosvdWs carve_hosvd(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, int64_t k1,
-                    int64_t k2) {
+                    int64_t k2, bool want_pc = true) {
   HosvdWs h;
-  h.d = carve_decomp(c, l, m, n, p, false);
+  h.d = carve_decomp(c, l, m, n, p, false, want_pc);
   const int64_t k = k1 < k2 ? k1 : k2;
   const int64_t d = l > m ? l : m;
   h.Uk = c.take<float>(p * l * k);
@@ -209,6 +240,7 @@ struct Opts {
   float q_tol = 1e-5f;
   int32_t check_finite = 0;
   float jacobi_tol = 0.f;
+  int32_t precond = 0;
 };
 
 Opts read_opts(const pp_opts *o) {
@@ -219,6 +251,7 @@ Opts read_opts(const pp_opts *o) {
     if (o->q_tol > 0.f) r.q_tol = o->q_tol;
     r.check_finite = o->check_finite;
     r.jacobi_tol = o->jacobi_tol;
+    r.precond = o->precond;
   }
   return r;
 }
@@ -242,19 +275,32 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
   PP_TRY(pp::launch_sum_partials(w.part_h, np_h, w.scal + 1, st));
   stage(1, st);
-  // step 3: facewise SVD
+  // step 3: facewise SVD -- one-sided Jacobi, on the rows of R from a QR with
+  // column pivoting of each slice where the slice fits that kernel
   pp::JacobiArgs ja;
-  ja.X = w.Ah;
   ja.W = w.W;
   ja.sig = w.sig;
   ja.perm = w.perm;
   ja.sweeps = w.sweeps;
   ja.status = w.status;
-  ja.l = l;
-  ja.m = m;
   ja.p = p;
+  ja.key_l = l;
+  ja.key_m = m;
   ja.max_sweeps = o.max_sweeps;
-  ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(l, m);
+  if (w.pc) {
+    const int64_t b = l < m ? l : m;
+    pp::QrArgs qa{w.Ah, w.R, w.qperm, l, m, p};
+    PP_TRY(pp::launch_qrcp(qa, st));
+    ja.X = w.R;
+    ja.l = b;
+    ja.m = b;
+    ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(b, b);
+  } else {
+    ja.X = w.Ah;
+    ja.l = l;
+    ja.m = m;
+    ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(l, m);
+  }
   PP_TRY(pp::launch_jacobi(ja, st));
   stage(2, st);
   return PP_OK;
@@ -456,20 +502,11 @@ pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m, int6
   const Opts o = read_opts(opts);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
-  const DecompWs w = carve_decomp(c, l, m, n, p, false);
+  const DecompWs w = carve_decomp(c, l, m, n, p, false, o.precond >= 0);
   stage(0, st);
   if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
   stage(3, st);
-  pp::FactorArgs fa;
-  fa.X = w.Ah;
-  fa.W = w.W;
-  fa.sig = w.sig;
-  fa.perm = w.perm;
-  fa.l = l;
-  fa.m = m;
-  fa.p = p;
-  fa.b = b;
-  fa.a_pad = pp::jacobi_apad(l, m);
+  pp::FactorArgs fa = decomp_factor_args(w, l, m, p);
   fa.kfix = k;
   fa.rho = nullptr;
   fa.offs = nullptr;
@@ -518,7 +555,7 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
   const Opts o = read_opts(opts);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
-  const DecompWs w = carve_decomp(c, l, m, n, p, true);
+  const DecompWs w = carve_decomp(c, l, m, n, p, true, o.precond >= 0);
   stage(0, st);
   if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
   // Alg. 4.2 steps 4-7
@@ -536,16 +573,7 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
   PP_TRY(pp::launch_select(sa, st));
   stage(3, st);
   // step 8: truncated factors (packed) and the rebuild
-  pp::FactorArgs fa;
-  fa.X = w.Ah;
-  fa.W = w.W;
-  fa.sig = w.sig;
-  fa.perm = w.perm;
-  fa.l = l;
-  fa.m = m;
-  fa.p = p;
-  fa.b = b;
-  fa.a_pad = pp::jacobi_apad(l, m);
+  pp::FactorArgs fa = decomp_factor_args(w, l, m, p);
   fa.kfix = 0;
   fa.rho = rho;
   fa.offs = offs;
@@ -632,22 +660,12 @@ pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m, in
   const Opts o = read_opts(opts);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
-  const HosvdWs h = carve_hosvd(c, l, m, n, p, k1, k2);
+  const HosvdWs h = carve_hosvd(c, l, m, n, p, k1, k2, o.precond >= 0);
   const DecompWs &w = h.d;
-  const int64_t b = l < m ? l : m;
   const int64_t k = k1 < k2 ? k1 : k2;
   // (1) *Q-SVD with k = min(k1, k2) (Alg. 4.1), its error in scal[2]
   if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
-  pp::FactorArgs fa;
-  fa.X = w.Ah;
-  fa.W = w.W;
-  fa.sig = w.sig;
-  fa.perm = w.perm;
-  fa.l = l;
-  fa.m = m;
-  fa.p = p;
-  fa.b = b;
-  fa.a_pad = pp::jacobi_apad(l, m);
+  pp::FactorArgs fa = decomp_factor_args(w, l, m, p);
   fa.kfix = k;
   fa.rho = nullptr;
   fa.offs = nullptr;

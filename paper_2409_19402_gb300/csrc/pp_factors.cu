@@ -9,6 +9,10 @@
 // so no rotation accumulator is needed in the Jacobi kernel.  For a zero
 // singular value both vectors are returned as zero.
 //
+// With the QR preconditioner (pp_qrcp.cu) the roles swap: the Jacobi vectors
+// are the short-side singular vectors (scaled, in pivoted order) and the
+// long-side vector is long_q = X^T short_q / sigma_q.
+//
 // Rank per slice: R_t = k (fixed, Alg. 4.1) or rho_t (Alg. 4.2, packed at
 // offs[t]).  Output layouts (row-major blocks):
 //   fixed:  Uh[t] is l x k at t*l*k, Vh[t] is m x k at t*m*k, s at t*k
@@ -128,6 +132,93 @@ __global__ void __launch_bounds__(256) factor_short_kernel(FactorArgs a) {
   }
 }
 
+// QR-preconditioned Jacobi (pp_qrcp.cu): the converged rows of W have length
+// b and hold the short-side vectors in pivoted order,
+// W_q[j] = sigma_q u_q[qperm[j]]; one CTA per slice.
+__global__ void factor_pc_short_kernel(FactorArgs a) {
+  const int64_t t = blockIdx.x;
+  const Geo g = geo(a, t);
+  const bool rows = a.l <= a.m;
+  float *out = rows ? a.Uh + g.uoff : a.Vh + g.voff;
+  const float *sg = a.sig + t * a.b;
+  const int32_t *pm = a.perm + t * a.b;
+  const int32_t *qp = a.qperm + t * a.b;
+  const float *Wt = a.W + t * a.b * a.a_pad;
+  for (int64_t idx = threadIdx.x; idx < a.b * g.rank; idx += blockDim.x) {
+    const int64_t j = idx / g.rank, q = idx % g.rank;
+    const float sq = sg[q];
+    out[(int64_t)qp[j] * g.rank + q] = sq > 0.f ? Wt[(int64_t)pm[q] * a.a_pad + j] / sq : 0.f;
+  }
+  for (int64_t q = threadIdx.x; q < g.rank; q += blockDim.x) a.s[g.soff + q] = sg[q];
+  if (threadIdx.x == 0 && a.kept_partial) {
+    double kept = 0.0, disc = 0.0;
+    for (int64_t q = 0; q < a.b; ++q) {
+      const double v = (double)sg[q] * (double)sg[q];
+      if (q < g.rank) kept += v; else disc += v;
+    }
+    a.kept_partial[t] = kept;
+    a.disc_partial[t] = disc;
+  }
+}
+
+// ... and the long-side vectors from the slice: long_q(e) = sum_{e2} X(e2, e)
+// u_q(e2) / sigma_q over the short index e2 (X oriented short x long);
+// tile 64 (e) x 32 (q), 256 threads, each 4 x 2 outputs.
+__global__ void __launch_bounds__(256) factor_pc_long_kernel(FactorArgs a) {
+  const int64_t t = blockIdx.z;
+  const Geo g = geo(a, t);
+  const bool rows = a.l <= a.m;
+  const int64_t nshort = rows ? a.l : a.m, nlong = rows ? a.m : a.l;
+  const int64_t e0 = (int64_t)blockIdx.y * 64, q0 = (int64_t)blockIdx.x * 32;
+  if (e0 >= nlong || q0 >= g.rank) return;
+  __shared__ float Xs[16][64 + 1];
+  __shared__ float Us[16][32 + 1];
+  const float *Xf = a.X + t * a.l * a.m;
+  const float *sg = a.sig + t * a.b;
+  const float *U = rows ? a.Uh + g.uoff : a.Vh + g.voff;      // nshort x rank
+  const int tid = threadIdx.x, ti = tid / 16, tj = tid % 16;
+  float acc[4][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+  for (int64_t k0 = 0; k0 < nshort; k0 += 16) {
+    for (int e = tid; e < 64 * 16; e += 256) {
+      int ii, kk;
+      if (rows) { ii = e % 64; kk = e / 64; } else { kk = e % 16; ii = e / 16; }
+      const int64_t e2 = k0 + kk, el = e0 + ii;
+      float v = 0.f;
+      if (e2 < nshort && el < nlong) v = rows ? Xf[e2 * a.m + el] : Xf[el * a.m + e2];
+      Xs[kk][ii] = v;
+    }
+    for (int e = tid; e < 32 * 16; e += 256) {
+      const int qq = e % 32, kk = e / 32;
+      const int64_t e2 = k0 + kk, q = q0 + qq;
+      Us[kk][qq] = (e2 < nshort && q < g.rank) ? U[e2 * g.rank + q] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float xv = Xs[kk][ti + 16 * r];
+        acc[r][0] = fmaf(xv, Us[kk][tj], acc[r][0]);
+        acc[r][1] = fmaf(xv, Us[kk][tj + 16], acc[r][1]);
+      }
+    }
+    __syncthreads();
+  }
+  float *out = rows ? a.Vh + g.voff : a.Uh + g.uoff;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t el = e0 + ti + 16 * r;
+    if (el >= nlong) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int64_t q = q0 + tj + 16 * c;
+      if (q >= g.rank) continue;
+      const float sq = sg[q];
+      out[el * g.rank + q] = sq > 0.f ? acc[r][c] / sq : 0.f;
+    }
+  }
+}
+
 // rebuild: Ahk(i, j) = sum_{q < R} Uh(i, q) s_q Vh(j, q); tile 64 x 64, 256 threads
 __global__ void __launch_bounds__(256) rebuild_kernel(FactorArgs a) {
   const int64_t t = blockIdx.z;
@@ -179,6 +270,22 @@ __global__ void __launch_bounds__(256) rebuild_kernel(FactorArgs a) {
 
 cudaError_t launch_factors(const FactorArgs &a, cudaStream_t st) {
   const int64_t R = a.kfix > 0 ? a.kfix : a.b;   // grid bound; ragged CTAs exit early
+  if (a.qperm) {
+    count_launch(1);
+    factor_pc_short_kernel<<<(unsigned)a.p, 256, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nlong = a.l <= a.m ? a.m : a.l;
+    const dim3 g1((unsigned)((R + 31) / 32), (unsigned)((nlong + 63) / 64), (unsigned)a.p);
+    count_launch(1);
+    factor_pc_long_kernel<<<g1, 256, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !a.Ahk) return e;
+    const dim3 g2((unsigned)((a.m + 63) / 64), (unsigned)((a.l + 63) / 64), (unsigned)a.p);
+    count_launch(1);
+    rebuild_kernel<<<g2, 256, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   count_launch(1);
   factor_long_kernel<<<(unsigned)a.p, 256, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();

@@ -67,15 +67,16 @@ cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64
 
 // ---------------------------------------------------------------- Jacobi
 struct JacobiArgs {
-  const float *X;     // p faces, l x m row-major each (transform domain A-hat)
-  float *W;           // p * b * a_pad: rotated vectors (output / blocked store)
-  float *sig;         // p * b: singular values, descending per face
-  int32_t *perm;      // p * b: sorted position -> vector index
-  int32_t *sweeps;    // p: sweeps used per face
-  int32_t *status;    // device status word
-  int64_t l, m, p;
-  int32_t max_sweeps;
-  float tol;          // rotation threshold on |cos|
+  const float *X = nullptr;   // p faces, l x m row-major each (transform domain A-hat)
+  float *W = nullptr;         // p * b * a_pad: rotated vectors (output / blocked store)
+  float *sig = nullptr;       // p * b: singular values, descending per face
+  int32_t *perm = nullptr;    // p * b: sorted position -> vector index
+  int32_t *sweeps = nullptr;  // p: sweeps used per face
+  int32_t *status = nullptr;  // device status word
+  int64_t l = 0, m = 0, p = 0;
+  int32_t max_sweeps = 30;
+  float tol = 0.f;            // rotation threshold on |cos|
+  int64_t key_l = 0, key_m = 0;   // slice shape for registered launch shapes (0: l, m)
 };
 int64_t jacobi_apad(int64_t l, int64_t m);
 // register (C >= 1) or remove (C = 0) the Jacobi launch shape for l x m slices, p of them
@@ -97,6 +98,19 @@ struct SelectArgs {
 cudaError_t launch_select(const SelectArgs &a, cudaStream_t st);
 
 // ---------------------------------------------------------------- factors / rebuild
+// ---------------------------------------------------------------- QR with column pivoting
+// Preconditioner of the Jacobi SVD: for each slice, the b = min(l, m) vectors
+// (rows if l <= m, else columns) as columns of Y: Y P = Q R.  R (p * b * b,
+// row-major upper triangular) becomes the Jacobi input; qperm[t * b + j] is the
+// original index of the vector in pivoted position j.  Q is not formed.
+struct QrArgs {
+  const float *X;
+  float *R;
+  int32_t *qperm;
+  int64_t l, m, p;
+};
+bool qrcp_fits(int64_t l, int64_t m);   // the slice fits the kernel's shared memory
+cudaError_t launch_qrcp(const QrArgs &a, cudaStream_t st);
 struct FactorArgs {
   const float *X;          // A-hat, p faces l x m
   const float *W;          // converged vectors, p * b * a_pad
@@ -110,6 +124,10 @@ struct FactorArgs {
   float *Ahk;              // rebuilt transform-domain tensor p x l x m
   double *kept_partial;    // per face kept sigma^2 (FP64) -> used for trunc report
   double *disc_partial;    // per face discarded sigma^2
+  // QR-preconditioned Jacobi (launch_qrcp): W holds the rotated rows of R (length
+  // b, a_pad = jacobi_apad(b, b)); the orthonormal side is then the short one,
+  // u_q[qperm[j]] = W_q[j] / sigma_q, and the long side is X^T u_q / sigma_q.
+  const int32_t *qperm = nullptr;
 };
 cudaError_t launch_factors(const FactorArgs &a, cudaStream_t st);
 

@@ -883,7 +883,8 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
   int regC = -1, regG = 0;
   {
     std::lock_guard<std::mutex> lock(g_shape_mu);
-    auto it = g_shapes.find(std::make_tuple(A.l, A.m, A.p));
+    auto it = g_shapes.find(std::make_tuple(A.key_l > 0 ? A.key_l : A.l,
+                                            A.key_m > 0 ? A.key_m : A.m, A.p));
     if (it != g_shapes.end()) { regC = it->second.first; regG = it->second.second; }
   }
   if (regC >= 2) {   // a registered cluster shape, if it can be launched

@@ -1,0 +1,260 @@
+// pp_qrcp.cu -- QR factorisation with column pivoting of every transform-domain
+// slice, the preconditioner of the one-sided Jacobi SVD (Drmac & Veselic,
+// "New fast and accurate Jacobi SVD algorithm", SIAM J. Matrix Anal. Appl.
+// 29 (2008)).
+//
+// A slice X (l x m) has b = min(l, m) vectors of length a = max(l, m): its rows
+// when l <= m, else its columns.  With Y the a x b matrix whose columns are
+// those vectors, Householder QR with column pivoting gives Y P = Q R (R b x b
+// upper triangular).  The Jacobi iteration then orthogonalises the rows of R:
+// graded, shorter (b instead of a) and much closer to orthogonal than the rows
+// of X, they converge in fewer sweeps.  Q is never formed: with J R = W
+// (orthogonal rows) the normalised rows of W are the short-side singular
+// vectors of X in pivoted order (W_k[j] = sigma_k u_k[perm[j]]), and the
+// long-side vectors follow from X itself (X^T u_k / sigma_k, pp_factors.cu).
+//
+// One CTA per slice holds Y in shared memory; vectors never move.  Step k:
+// every warp reduces the per-warp candidates left by the previous update to
+// the pivot (the unpivoted vector with the largest trailing norm, the lowest
+// index on ties) and forms the scalars of its Householder reflector; all
+// threads then apply the reflector to the unpivoted vectors, 4 lanes per
+// vector, recompute their trailing norms from the updated entries (no norm
+// downdating, hence no cancellation safeguard) and leave the next candidates.
+// One barrier per step; R is written at the end.
+#include "pp_internal.h"
+
+namespace pp {
+namespace {
+
+constexpr int QR_THREADS = 512;
+constexpr int QG = 4;                        // lanes per vector in the update
+constexpr int QR_SMEM_BUDGET = 200 * 1024;
+
+// row stride of the vector store: a multiple of 4 floats (float4 access) that
+// is 16 mod 32, so the 4-lane groups of a warp alternate between the two
+// halves of the banks
+__host__ __device__ inline int64_t qr_ap(int64_t a) { return (a + 31) / 32 * 32 + 16; }
+
+__host__ __device__ inline int64_t qr_smem_floats(int64_t b, int64_t a) {
+  return b * qr_ap(a) + 3 * b;               // vectors, diagonal, used flags, order
+}
+
+constexpr int QR_NREG = 12;                  // float4 per lane held in registers in the update
+
+// y -= f h on a float4; the squared entries above k join the trailing norm
+// (four partial sums; masked only in the float4 that holds entry k)
+__device__ __forceinline__ void qr_update4(float4 &v, const float4 h, float f, int e, int k,
+                                           bool edge, float4 &s) {
+  v.x = fmaf(-f, h.x, v.x);
+  v.y = fmaf(-f, h.y, v.y);
+  v.z = fmaf(-f, h.z, v.z);
+  v.w = fmaf(-f, h.w, v.w);
+  if (edge) {
+    s.x = fmaf(e + 0 > k ? v.x : 0.f, v.x, s.x);
+    s.y = fmaf(e + 1 > k ? v.y : 0.f, v.y, s.y);
+    s.z = fmaf(e + 2 > k ? v.z : 0.f, v.z, s.z);
+    s.w = fmaf(e + 3 > k ? v.w : 0.f, v.w, s.w);
+  } else {
+    s.x = fmaf(v.x, v.x, s.x);
+    s.y = fmaf(v.y, v.y, s.y);
+    s.z = fmaf(v.z, v.z, s.z);
+    s.w = fmaf(v.w, v.w, s.w);
+  }
+}
+
+// Warp-wide choice among (norm, vector) candidates: the largest norm, the lowest
+// vector index on ties; lanes without a candidate pass j = QR_NONE.  Norms are
+// >= 0, so their bit patterns order like the values.
+constexpr unsigned QR_NONE = 0x7fffffffu;
+__device__ __forceinline__ void warp_pivot(float v, unsigned j, unsigned &bv, unsigned &bj) {
+  const unsigned bits = j == QR_NONE ? 0u : __float_as_uint(v);
+  bv = __reduce_max_sync(0xffffffffu, bits);
+  bj = __reduce_min_sync(0xffffffffu, (j != QR_NONE && bits == bv) ? j : QR_NONE);
+}
+
+// the reflector's float4 at e4: the pivot vector's entries, with 0 below k and
+// vk at k (only the float4 holding entry k differs)
+__device__ __forceinline__ float4 qr_h4(const float4 *p4, int e4, int k4, int k, float vk) {
+  float4 h = p4[e4];
+  if (e4 == k4) {
+    const int e = 4 * e4;
+    h.x = e + 0 < k ? 0.f : (e + 0 == k ? vk : h.x);
+    h.y = e + 1 < k ? 0.f : (e + 1 == k ? vk : h.y);
+    h.z = e + 2 < k ? 0.f : (e + 2 == k ? vk : h.z);
+    h.w = e + 3 < k ? 0.f : (e + 3 == k ? vk : h.w);
+  }
+  return h;
+}
+
+__global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
+  extern __shared__ __align__(16) float qs[];
+  constexpr int NW = QR_THREADS / 32;
+  __shared__ unsigned cand_v[2][NW], cand_j[2][NW];   // pivot candidates per warp, by step parity
+  const int64_t f = blockIdx.x;
+  const int l = (int)A.l, m = (int)A.m;
+  const bool rows = l <= m;
+  const int b = rows ? l : m, a = rows ? m : l;
+  const int ap = (int)qr_ap(a), ap4 = ap / 4;
+  float *Y = qs;                             // vector j (original index) at Y + j * ap
+  float *diag = Y + (size_t)b * ap;          // R(k, k)
+  int *used = reinterpret_cast<int *>(diag + b);   // vector j already pivoted
+  int *order = used + b;                     // pivoted position -> vector
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int glane = tid % QG, grp = tid / QG, ngrp = QR_THREADS / QG;
+  const unsigned gmask = ((1u << QG) - 1u) << (lane & ~(QG - 1));
+  const float *Xf = A.X + f * (int64_t)l * m;
+
+  if (rows) {
+    for (int idx = tid; idx < b * ap; idx += QR_THREADS) {
+      const int j = idx / ap, e = idx % ap;
+      Y[idx] = e < a ? Xf[(int64_t)j * m + e] : 0.f;
+    }
+  } else {
+    for (int idx = tid; idx < b * a; idx += QR_THREADS) {
+      const int e = idx / b, j = idx % b;
+      Y[(size_t)j * ap + e] = Xf[(int64_t)e * m + j];
+    }
+    for (int idx = tid; idx < b * (ap - a); idx += QR_THREADS)
+      Y[(size_t)(idx / (ap - a)) * ap + a + idx % (ap - a)] = 0.f;
+  }
+  for (int j = tid; j < b; j += QR_THREADS) used[j] = 0;
+  __syncthreads();
+  {
+    float bestv = 0.f;
+    unsigned bestj = QR_NONE;
+    for (int j = grp; j < b; j += ngrp) {
+      const float4 *y4 = reinterpret_cast<const float4 *>(Y + (size_t)j * ap);
+      float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int e4 = glane; e4 < ap4; e4 += QG) {
+        const float4 v = y4[e4];
+        s4.x = fmaf(v.x, v.x, s4.x);
+        s4.y = fmaf(v.y, v.y, s4.y);
+        s4.z = fmaf(v.z, v.z, s4.z);
+        s4.w = fmaf(v.w, v.w, s4.w);
+      }
+      float s = (s4.x + s4.y) + (s4.z + s4.w);
+#pragma unroll
+      for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
+      if (bestj == QR_NONE || s > bestv) { bestv = s; bestj = (unsigned)j; }
+    }
+    unsigned bv, bj;
+    warp_pivot(bestv, bestj, bv, bj);
+    if (lane == 0) { cand_v[0][warp] = bv; cand_j[0][warp] = bj; }
+  }
+  __syncthreads();
+
+  // One barrier per step: every warp reduces the candidates left by the last
+  // update (double-buffered by step parity) to the same pivot sp and computes
+  // the reflector's scalars itself; the pivot vector is never written (its
+  // entries above k are R's column, entry k becomes vk only inside qr_h4).
+  for (int k = 0; k < b; ++k) {
+    const int k4 = k / 4;
+    const int par = k & 1;
+    unsigned bv, bj;
+    warp_pivot(lane < NW ? __uint_as_float(cand_v[par][lane]) : 0.f,
+               lane < NW ? cand_j[par][lane] : QR_NONE, bv, bj);
+    const int sp = bj < (unsigned)b ? (int)bj : 0;
+    // Householder reflector H = I - beta v v^T with H y = alpha e_k:
+    // alpha = -sign(y_k) |y|, v = y - alpha e_k, v^T v = 2 |y| (|y| + |y_k|),
+    // |y|^2 = the pivot's trailing norm (entries k..a-1)
+    const float4 *p4 = reinterpret_cast<const float4 *>(Y + (size_t)sp * ap);
+    const float x0 = Y[(size_t)sp * ap + k];
+    const float nx = sqrtf(__uint_as_float(bv));
+    const float alpha = x0 >= 0.f ? -nx : nx;
+    const float vk = x0 - alpha;
+    const float vtv = 2.f * nx * (nx + fabsf(x0));
+    const float beta = vtv > 0.f ? __fdividef(2.f, vtv) : 0.f;
+    if (tid == 0) {
+      diag[k] = alpha;
+      used[sp] = 1;
+      order[k] = sp;
+    }
+    const bool in_regs = ap4 - k4 <= QG * QR_NREG;
+    float bestv = 0.f;
+    unsigned bestj = QR_NONE;
+    for (int j = grp; j < b; j += ngrp) {
+      if (j == sp || used[j]) continue;
+      float4 *y4 = reinterpret_cast<float4 *>(Y + (size_t)j * ap);
+      float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f), s4 = c4;
+      if (in_regs) {                           // one read and one write of the vector
+        float4 r[QR_NREG];
+#pragma unroll
+        for (int q = 0; q < QR_NREG; ++q) {
+          const int e4 = k4 + glane + QG * q;
+          if (e4 < ap4) {
+            r[q] = y4[e4];
+            const float4 h = qr_h4(p4, e4, k4, k, vk);
+            c4.x = fmaf(h.x, r[q].x, c4.x);
+            c4.y = fmaf(h.y, r[q].y, c4.y);
+            c4.z = fmaf(h.z, r[q].z, c4.z);
+            c4.w = fmaf(h.w, r[q].w, c4.w);
+          }
+        }
+        float c = (c4.x + c4.y) + (c4.z + c4.w);
+#pragma unroll
+        for (int o = QG / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, QG);
+        const float fct = beta * c;
+#pragma unroll
+        for (int q = 0; q < QR_NREG; ++q) {
+          const int e4 = k4 + glane + QG * q;
+          if (e4 < ap4) {
+            qr_update4(r[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
+            y4[e4] = r[q];
+          }
+        }
+      } else {                                 // long vectors: a read pass, then read-write
+        for (int e4 = k4 + glane; e4 < ap4; e4 += QG) {
+          const float4 h = qr_h4(p4, e4, k4, k, vk), v = y4[e4];
+          c4.x = fmaf(h.x, v.x, c4.x);
+          c4.y = fmaf(h.y, v.y, c4.y);
+          c4.z = fmaf(h.z, v.z, c4.z);
+          c4.w = fmaf(h.w, v.w, c4.w);
+        }
+        float c = (c4.x + c4.y) + (c4.z + c4.w);
+#pragma unroll
+        for (int o = QG / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, QG);
+        const float fct = beta * c;
+        for (int e4 = k4 + glane; e4 < ap4; e4 += QG) {
+          float4 v = y4[e4];
+          qr_update4(v, qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
+          y4[e4] = v;
+        }
+      }
+      float s = (s4.x + s4.y) + (s4.z + s4.w);
+#pragma unroll
+      for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
+      if (bestj == QR_NONE || s > bestv) { bestv = s; bestj = (unsigned)j; }
+    }
+    warp_pivot(bestv, bestj, bv, bj);
+    if (lane == 0) { cand_v[par ^ 1][warp] = bv; cand_j[par ^ 1][warp] = bj; }
+    __syncthreads();
+  }
+  // R(i, j) for j > i: entry i of the vector at pivoted position j (final
+  // after step i); the diagonal from diag
+  float *Rf = A.R + f * (int64_t)b * b;
+  for (int idx = tid; idx < b * b; idx += QR_THREADS) {
+    const int i = idx / b, j = idx % b;
+    Rf[idx] = j < i ? 0.f : (j == i ? diag[j] : Y[(size_t)order[j] * ap + i]);
+  }
+  for (int j = tid; j < b; j += QR_THREADS) A.qperm[f * b + j] = order[j];
+}
+
+}  // namespace
+
+bool qrcp_fits(int64_t l, int64_t m) {
+  const int64_t b = l < m ? l : m, a = l < m ? m : l;
+  return b >= 2 && (int64_t)sizeof(float) * qr_smem_floats(b, a) <= QR_SMEM_BUDGET;
+}
+
+cudaError_t launch_qrcp(const QrArgs &A, cudaStream_t st) {
+  const int64_t b = A.l < A.m ? A.l : A.m, a = A.l < A.m ? A.m : A.l;
+  const size_t smem = sizeof(float) * (size_t)qr_smem_floats(b, a);
+  cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch(1);
+  qrcp_kernel<<<(unsigned)A.p, QR_THREADS, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace pp

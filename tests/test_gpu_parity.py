@@ -185,10 +185,10 @@ def _margin(sig_ref, gamma, K):
     return min(c[K - 1] - gamma * cN, gamma * cN - lo) / cN, keys
 
 
-def _tsvdqII_case(A, Q, gamma):
+def _tsvdqII_case(A, Q, gamma, **opts):
     b = _b()
-    out = b.tsvdqII(dev(A), dev(Q), gamma)
-    full = b.tsvdq_trunc(dev(A), dev(Q), min(A.shape[1], A.shape[2]), want_ak=False)
+    out = b.tsvdqII(dev(A), dev(Q), gamma, **opts)
+    full = b.tsvdq_trunc(dev(A), dev(Q), min(A.shape[1], A.shape[2]), want_ak=False, **opts)
     torch.cuda.synchronize()
     rep = out.report()
     assert rep.status == 0, b.status_str(rep.status)
@@ -222,6 +222,17 @@ def _tsvdqII_case(A, Q, gamma):
         np.testing.assert_allclose((Ut * st) @ Vt.T, (ref.Uh[t] * ref.s[t]) @ ref.Vh[t].T,
                                    atol=2e-5 * ref.sig_all[t, 0])
     return rep, ref
+
+
+@pytest.mark.parametrize("precond", [True, False])
+@pytest.mark.parametrize("shape", [(40, 23, 57), (40, 57, 23), (24, 33, 33), (64, 130, 9)])
+def test_tsvdqII_with_and_without_qr_preconditioner(shape, precond):
+    """Both Jacobi paths (rows of R from the QR with column pivoting, or the
+    slice itself) against the oracle, on wide, tall, square and very flat slices."""
+    n, l, m = shape
+    A = inputs.gaussian(shape, seed=31 + l)
+    Q = inputs.random_q(n, 12, seed=32)
+    _tsvdqII_case(A, Q, 0.9, precond=precond)
 
 
 def test_tsvdqII_tiny():
