@@ -50,19 +50,25 @@ def nominal_svd_flops(l, m, p):
     return p * (4.0 * a * b * b + 8.0 * b ** 3)
 
 
-def jacobi_traffic():
-    """DRAM bytes per launch of the Jacobi kernel from the committed ncu capture,
-    or None when the kernel source has changed since that capture."""
+def stage_traffic(kernels):
+    """DRAM bytes per launch of the SVD stage's kernels from the committed ncu
+    captures (summed), or None when any kernel's source has changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     try:
         with open(path) as f:
-            rec = json.load(f)["jacobi_cluster_kernel"]
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+            recs = json.load(f)
+        total = 0
+        for k in kernels:
+            rec = recs[k]
+            with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+                sha = hashlib.sha256(f.read()).hexdigest()
+            if not sha.startswith(rec["sha256_prefix"]):
+                return None
+            total += rec["dram_bytes_per_launch"]
+        return total
     except (OSError, KeyError, ValueError):
         return None
-    return rec["dram_bytes_per_launch"] if sha.startswith(rec["sha256_prefix"]) else None
 
 
 def load_peaks():
@@ -279,7 +285,12 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     # launch-shape autotuning of the Jacobi SVD on this problem (setup, untimed)
     from paper_2409_19402_gb300 import autotune
-    tuned = autotune.tune_jacobi(A_d, Qp_d, gamma=GAMMA, use_cache=False)
+    if args.jacobi_shape:                          # fixed shape (profiling runs)
+        C, GW, pc = (int(x) for x in args.jacobi_shape.split(","))
+        binding.set_jacobi_shape(L, M, P, C, GW)
+        tuned = (C, GW, None, bool(pc))
+    else:
+        tuned = autotune.tune_jacobi(A_d, Qp_d, gamma=GAMMA, use_cache=False)
     tuned_n = autotune.tune_jacobi(A_d, Qn_d, gamma=GAMMA, use_cache=False) if not args.no_pn else None
     run = Runner(A_d, Qp_d, GAMMA, torch, binding, precond=tuned[3])
 
@@ -328,9 +339,10 @@ def run_ours(args):
     jac_ms = stage_mean[1]
     flops = nominal_svd_flops(L, M, P)
     achieved = flops / (jac_ms / 1e3) / 1e12
-    roofline = {"kernel": "jacobi_cluster_kernel (facewise one-sided Jacobi SVD)", "bound": "alu",
+    stage_kernels = (["qrcp_kernel"] if tuned[3] else []) + ["jacobi_cluster_kernel"]
+    roofline = {"kernel": " + ".join(stage_kernels) + " (facewise SVD stage)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": jacobi_traffic(),
+                "frac": achieved / fp32_peak, "traffic": stage_traffic(stage_kernels),
                 "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                              f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
                 "work": "nominal 4ab^2+8b^3 per slice (Golub-Kahan-Reinsch), p=50"}
@@ -553,6 +565,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--jacobi-shape", default="",
+                    help="C,GW,precond: fixed Jacobi launch shape instead of autotuning")
     ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
