@@ -18,7 +18,8 @@ Workloads (stand-ins for the paper's datasets, which are not available here):
                  (shape class of Indian Pines, Sec. 5.3)
   batched        64 Tucker-rank-10 tensors of uneven sizes + noise         seed 3
 Transformation matrices (Sec. 5.1.1): DCT-II, random orthonormal, and U3 (the
-leading left singular vectors of the mode-3 unfolding, Thm. 4.3).
+leading left singular vectors of the mode-3 unfolding, Thm. 4.3); complex
+ones (Sec. 3, Q in St_{n,p}(C)): the DFT rows and a random complex Q.
 """
 from __future__ import annotations
 
@@ -149,6 +150,29 @@ def dct_q(n: int, p: int) -> np.ndarray:
     t = np.arange(p, dtype=np.float64)[None, :]
     c = np.where(t == 0, math.sqrt(1.0 / n), math.sqrt(2.0 / n))
     return (c * np.cos(math.pi * (2.0 * s + 1.0) * t / (2.0 * n))).astype(np.float32)
+
+
+def dft_qc(n: int, p: int) -> np.ndarray:
+    """Complex Q = F(1:p, :)^H for the unitary DFT matrix F (F[t, s] =
+    exp(-2 pi i t s / n) / sqrt(n)): Q[s, t] = exp(+2 pi i s t / n) / sqrt(n),
+    complex64 (n, p) -- the t-product-like transformation (p = n: the t-product
+    up to the factor 1/sqrt(n))."""
+    s = np.arange(n, dtype=np.float64)[:, None]
+    t = np.arange(p, dtype=np.float64)[None, :]
+    ang = 2.0 * math.pi * ((s * t) % n) / n
+    return ((np.cos(ang) + 1j * np.sin(ang)) / math.sqrt(n)).astype(np.complex64)
+
+
+def random_qc(n: int, p: int, seed: int) -> np.ndarray:
+    """Random complex Q with orthonormal columns: the first p columns of the
+    unitary factor of an n x n complex Gaussian matrix (FP64 QR, column phases
+    fixed so that R has a non-negative real diagonal), complex64 (n, p)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    Qf, R = np.linalg.qr(G)
+    d = np.diag(R)
+    Qf = Qf * (np.conj(d) / np.abs(d))[None, :]
+    return np.ascontiguousarray(Qf[:, :p]).astype(np.complex64)
 
 
 def random_q(n: int, p: int, seed: int) -> np.ndarray:
