@@ -390,6 +390,11 @@ def run_ours(args):
     if world == 1 and not args.no_diff:
         diff = run_diff(args, torch, stream, dev)
 
+    # ---------------- complex transformation: DFT rows, p = 50 (tsvdqII_c)
+    cplx = None
+    if world == 1 and not args.no_complex:
+        cplx = run_complex(args, torch, binding, A_d, stream, dev)
+
     # ---------------- end to end through host buffers (pinned)
     e2e = None
     if not args.no_e2e:
@@ -406,7 +411,32 @@ def run_ours(args):
                "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
                "seconds": dt}
     return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-                  per_step_launches, clk, t_wall, dist, tuned, batched, diff)
+                  per_step_launches, clk, t_wall, dist, tuned, batched, diff, cplx)
+
+
+def run_complex(args, torch, binding, A_d, stream, dev):
+    """The video workload with a complex Q: the first p = 50 DFT rows
+    (Q = F(1:p,:)^H), *Q-SVDII with gamma = 0.99 through tsvdqII_c."""
+    from paper_2409_19402_gb300 import inputs
+    Qc = torch.from_numpy(inputs.dft_qc(N, P)).to(dev)
+    ws = binding.workspace(binding.workspace_bytes(binding.PP_OP_TSVDQII_C, l=L, m=M, n=N, p=P),
+                           dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            out = binding.tsvdqII_c(A_d, Qc, GAMMA, ws=ws, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            out = binding.tsvdqII_c(A_d, Qc, GAMMA, ws=ws, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    r = out.report()
+    return {"q": "DFT rows F(1:50,:)^H (complex)", "gamma": GAMMA, "ms_per_step": ms,
+            "value": L * M * N / (ms / 1e3), "unit": UNIT, "kappa": int(r.kappa),
+            "sweeps": int(r.sweeps), "RE": math.sqrt(r.err2 / r.normA2),
+            "status_ok": r.status == 0}
 
 
 def run_diff(args, torch, stream, dev):
@@ -529,7 +559,7 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-           per_step_launches, clk, t_wall, dist, tuned=None, batched=None, diff=None):
+           per_step_launches, clk, t_wall, dist, tuned=None, batched=None, diff=None, cplx=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -547,6 +577,7 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
             "pn_compare": pn,
             "batched_64": batched,
             "diff_step": diff,
+            "complex_dft": cplx,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "gpu_launches": int(round(per_step_launches * args.steps)),
@@ -565,6 +596,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-complex", action="store_true")
     ap.add_argument("--jacobi-shape", default="",
                     help="C,GW,precond: fixed Jacobi launch shape instead of autotuning")
     ap.add_argument("--no-pn", action="store_true", help="skip the p = n comparison")

@@ -78,7 +78,10 @@ typedef enum pp_op {
     PP_OP_TSVDQII = 4,
     PP_OP_HOSVD = 5,
     PP_OP_PPROD_BWD = 6,
-    PP_OP_U3 = 7
+    PP_OP_U3 = 7,
+    PP_OP_PPROD_C = 8,
+    PP_OP_TSVDQ_C = 9,
+    PP_OP_TSVDQII_C = 10
 } pp_op;
 
 /* Problem sizes for pp_workspace_bytes.  Fields an op does not use are
@@ -278,6 +281,44 @@ PP_API pp_status pp_hosvd_matched_k2(int64_t l, int64_t m, int64_t n, int64_t p,
 PP_API pp_status pprod_u3(const float *A, int64_t l, int64_t m, int64_t n, int64_t p, float *Q,
                           float *lambda, pp_report *rep, const pp_opts *opts, void *ws,
                           size_t ws_bytes, void *stream);
+
+/*
+ * Complex transformations (Sec. 3: Q in St_{n,p}(C), Q^H Q = I_p; the remark
+ * after Def. 3.2: with Q = F(1:p,:)^H, rows of the unitary DFT, the product
+ * of real tensors can be complex).  The data A, B are REAL (as in the paper's
+ * experiments); Q is complex, interleaved (Q[2 (s p + t)] = Re Q(s, t),
+ * Q[2 (s p + t) + 1] = Im Q(s, t), i.e. C99 float complex / torch.complex64,
+ * row-major n x p).  The transform domain A x_3 Q^H is complex; its facewise
+ * SVDs use a one-sided Jacobi with unitary 2 x 2 rotations (the pair's phase,
+ * then the real rotation), singular values real and sorted descending.
+ * Complex factors are interleaved with the layouts of the real entry points;
+ * complex tensor outputs are given as separate real and imaginary arrays.
+ * pp_report fields as for the real calls: err2 = |A - Re A_k|^2 + |Im A_k|^2.
+ * opts: max_sweeps, jacobi_tol, check_finite (A) and check_q (max |Q^H Q - I|)
+ * apply; precond does not (no QR preconditioner on this path).  Slices must
+ * fit one CTA's shared memory: min(l,m) * roundup(max(l,m), 16) * 8 bytes
+ * <= 200 KB, else PP_ENOSYS (the video-shaped 120 x 160 slices fit).
+ *
+ * pprod_c: C = A *Q B (Def. 3.1 over C), A n1 x m x n, B m x n2 x n real,
+ *   C_re, C_im (n1 x n2 x n each).  Workspace PP_OP_PPROD_C {l = n1, m, n, p, n2}.
+ * tsvdq_trunc_c: Alg. 4.1 over C; Uh (p, l, k) and Vh (p, m, k) complex,
+ *   s (p, k); Ak_re / Ak_im both NULL or both given.  Workspace PP_OP_TSVDQ_C.
+ * tsvdqII_c: Alg. 4.2 over C; rho, offs as tsvdqII; Uh_pk / Vh_pk complex
+ *   packed blocks (capacity p min(l,m) l and p min(l,m) m complex), s_pk real.
+ *   Workspace PP_OP_TSVDQII_C.
+ */
+PP_API pp_status pprod_c(const float *A, const float *B, const float *Q, int64_t n1, int64_t m,
+                         int64_t n2, int64_t n, int64_t p, float *C_re, float *C_im, void *ws,
+                         size_t ws_bytes, void *stream);
+PP_API pp_status tsvdq_trunc_c(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                               int64_t p, int64_t k, float *Uh, float *s, float *Vh,
+                               float *Ak_re, float *Ak_im, pp_report *rep, const pp_opts *opts,
+                               void *ws, size_t ws_bytes, void *stream);
+PP_API pp_status tsvdqII_c(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                           int64_t p, double gamma, int32_t *rho, int64_t *offs, float *Uh_pk,
+                           float *s_pk, float *Vh_pk, float *Ak_re, float *Ak_im,
+                           pp_report *rep, const pp_opts *opts, void *ws, size_t ws_bytes,
+                           void *stream);
 
 /*
  * Batched *Q-SVDII over independent tensors of uneven sizes (one item per

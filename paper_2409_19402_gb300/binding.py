@@ -25,6 +25,7 @@ PP_ETIMEOUT, PP_EWORKSPACE, PP_ECUDA, PP_ENOSYS = 6, 7, 8, 9
 PP_OP_MODE3, PP_OP_FACEWISE, PP_OP_PPROD, PP_OP_TSVDQ, PP_OP_TSVDQII, PP_OP_HOSVD = 0, 1, 2, 3, 4, 5
 PP_OP_PPROD_BWD = 6
 PP_OP_U3 = 7
+PP_OP_PPROD_C, PP_OP_TSVDQ_C, PP_OP_TSVDQII_C = 8, 9, 10
 
 
 class PPError(RuntimeError):
@@ -106,6 +107,13 @@ def lib() -> ctypes.CDLL:
         L.tsvdqII_noalloc.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp,
                                       vp, vp, vp, vp, ctypes.POINTER(pp_opts), vp]
         L.tsvdqII_noalloc.restype = i32
+        L.pprod_c.argtypes = [vp, vp, vp, i64, i64, i64, i64, i64, vp, vp, vp, sz, vp]
+        L.tsvdq_trunc_c.argtypes = [vp, vp, i64, i64, i64, i64, i64, vp, vp, vp, vp, vp, vp,
+                                    ctypes.POINTER(pp_opts), vp, sz, vp]
+        L.tsvdqII_c.argtypes = [vp, vp, i64, i64, i64, i64, ctypes.c_double, vp, vp, vp, vp, vp,
+                                vp, vp, vp, ctypes.POINTER(pp_opts), vp, sz, vp]
+        for f in ("pprod_c", "tsvdq_trunc_c", "tsvdqII_c"):
+            getattr(L, f).restype = i32
         L.pprod_u3.argtypes = [vp, i64, i64, i64, i64, vp, vp, vp, ctypes.POINTER(pp_opts), vp,
                                sz, vp]
         L.pprod_u3.restype = i32
@@ -381,6 +389,79 @@ def hosvd_compare(A: torch.Tensor, Q: torch.Tensor, k1: int, k2: int, want_ak: b
                                0 if ws is None else ws.numel(), _stream(stream)), "hosvd_compare")
     raw = bytes(rep.cpu().numpy().tobytes())
     return pp_hosvd_report.from_buffer_copy(raw), Ak
+
+
+def _check_c(t: torch.Tensor, name: str):
+    if not (t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
+
+
+def pprod_c(A: torch.Tensor, B: torch.Tensor, Q: torch.Tensor, ws=None, stream=None):
+    """Def. 3.1 with a complex Q (n, p) complex64 and real A (n, n1, m), B (n, m, n2);
+    returns (C_re, C_im), each (n, n1, n2)."""
+    _check_t(A, "A"); _check_t(B, "B"); _check_c(Q, "Q")
+    n, n1, m = A.shape
+    n2 = B.shape[2]
+    p = Q.shape[1]
+    dev = A.device
+    Cr = torch.empty((n, n1, n2), dtype=torch.float32, device=dev)
+    Ci = torch.empty((n, n1, n2), dtype=torch.float32, device=dev)
+    need = workspace_bytes(PP_OP_PPROD_C, l=n1, m=m, n=n, p=p, n2=n2)
+    if ws is None:
+        ws = workspace(need, dev)
+    _raise(lib().pprod_c(_ptr(A), _ptr(B), _ptr(Q), n1, m, n2, n, p, _ptr(Cr), _ptr(Ci), _ptr(ws),
+                         0 if ws is None else ws.numel(), _stream(stream)), "pprod_c")
+    return Cr, Ci
+
+
+def tsvdq_trunc_c(A: torch.Tensor, Q: torch.Tensor, k: int, want_ak: bool = True, ws=None,
+                  stream=None, **opts) -> TsvdqOut:
+    """Alg. 4.1 with a complex Q: Uh, Vh complex64; Ak = (Ak_re, Ak_im) or None."""
+    _check_t(A, "A"); _check_c(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    dev = A.device
+    Uh = torch.empty((p, l, k), dtype=torch.complex64, device=dev)
+    s = torch.empty((p, k), dtype=torch.float32, device=dev)
+    Vh = torch.empty((p, m, k), dtype=torch.complex64, device=dev)
+    Ak = ((torch.empty((n, l, m), dtype=torch.float32, device=dev),
+           torch.empty((n, l, m), dtype=torch.float32, device=dev)) if want_ak else (None, None))
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_TSVDQ_C, l=l, m=m, n=n, p=p, k=k)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().tsvdq_trunc_c(_ptr(A), _ptr(Q), l, m, n, p, int(k), _ptr(Uh), _ptr(s), _ptr(Vh),
+                               _ptr(Ak[0]), _ptr(Ak[1]), _ptr(rep), ctypes.byref(o), _ptr(ws),
+                               0 if ws is None else ws.numel(), _stream(stream)), "tsvdq_trunc_c")
+    return TsvdqOut(Uh, s, Vh, Ak if want_ak else None, rep)
+
+
+def tsvdqII_c(A: torch.Tensor, Q: torch.Tensor, gamma: float, want_ak: bool = True, ws=None,
+              stream=None, **opts) -> TsvdqIIOut:
+    """Alg. 4.2 with a complex Q: packed Uh, Vh complex64; Ak = (Ak_re, Ak_im) or None."""
+    _check_t(A, "A"); _check_c(Q, "Q")
+    n, l, m = A.shape
+    p = Q.shape[1]
+    r = min(l, m)
+    dev = A.device
+    rho = torch.empty(p, dtype=torch.int32, device=dev)
+    offs = torch.empty(p + 1, dtype=torch.int64, device=dev)
+    Uh = torch.empty(p * r * l, dtype=torch.complex64, device=dev)
+    s = torch.empty(p * r, dtype=torch.float32, device=dev)
+    Vh = torch.empty(p * r * m, dtype=torch.complex64, device=dev)
+    Ak = ((torch.empty((n, l, m), dtype=torch.float32, device=dev),
+           torch.empty((n, l, m), dtype=torch.float32, device=dev)) if want_ak else (None, None))
+    rep = torch.zeros(REPORT_BYTES, dtype=torch.uint8, device=dev)
+    need = workspace_bytes(PP_OP_TSVDQII_C, l=l, m=m, n=n, p=p)
+    if ws is None:
+        ws = workspace(need, dev)
+    o = _opts(**opts)
+    _raise(lib().tsvdqII_c(_ptr(A), _ptr(Q), l, m, n, p, float(gamma), _ptr(rho), _ptr(offs),
+                           _ptr(Uh), _ptr(s), _ptr(Vh), _ptr(Ak[0]), _ptr(Ak[1]), _ptr(rep),
+                           ctypes.byref(o), _ptr(ws), 0 if ws is None else ws.numel(),
+                           _stream(stream)), "tsvdqII_c")
+    return TsvdqIIOut(rho, offs, Uh, s, Vh, Ak if want_ak else None, rep, l, m)
 
 
 def pprod_u3(A: torch.Tensor, p: int, ws=None, stream=None, **opts):

@@ -317,6 +317,111 @@ pp_status backproject(const float *A, const float *Q, int64_t l, int64_t m, int6
   return PP_OK;
 }
 
+// ---- complex Q (pp_complex.cu)
+constexpr size_t CJ_SMEM_BUDGET = 200 * 1024;
+
+struct CDecompWs {
+  float *Pim, *Bre, *Bim;      // real matrices from Q
+  float *Ah, *Ahk;             // planar stacked transform domain (2 p l m each)
+  float2 *W;
+  float *sig;
+  int32_t *perm, *sweeps, *status, *rank;
+  double *kept_p, *disc_p, *part_a, *part_h, *part_e, *scal, *keys;
+  int64_t *K;
+};
+
+CDecompWs carve_cdecomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool ragged) {
+  const int64_t b = l < m ? l : m;
+  CDecompWs w{};
+  w.Pim = c.take<float>(p * n);
+  w.Bre = c.take<float>(2 * n * p);
+  w.Bim = c.take<float>(2 * n * p);
+  w.Ah = c.take<float>(2 * p * l * m);
+  w.Ahk = c.take<float>(2 * p * l * m);
+  w.W = c.take<float2>(p * b * pp::cjacobi_apad(l, m));
+  w.sig = c.take<float>(p * b);
+  w.perm = c.take<int32_t>(p * b);
+  w.sweeps = c.take<int32_t>(p);
+  w.kept_p = c.take<double>(p);
+  w.disc_p = c.take<double>(p);
+  w.part_a = c.take<double>(pp::mode3_tc_partials(p, l * m));
+  w.part_h = c.take<double>(2 * pp::mode3_tc_partials(p, l * m));
+  w.part_e = c.take<double>(2 * pp::mode3_tc_partials(n, l * m));
+  w.scal = c.take<double>(8);
+  w.status = c.take<int32_t>(1);
+  w.K = c.take<int64_t>(1);
+  if (ragged) {
+    w.keys = c.take<double>(p * b);
+    w.rank = c.take<int32_t>(p * b);
+  }
+  return w;
+}
+
+// A-hat = A x_3 Q^H (planar: Re = Re(Q)^T A, Im = -Im(Q)^T A) with |A|^2, |A-hat|^2,
+// then the complex facewise Jacobi SVD
+pp_status cproject_and_svd(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                           int64_t p, const Opts &o, const CDecompWs &w, cudaStream_t st) {
+  PP_TRY(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
+  if (o.check_q) PP_TRY(pp::launch_qc_check(Q, n, p, o.q_tol, w.status, st));
+  if (o.check_finite) PP_TRY(pp::launch_check_finite(A, n * l * m, w.status, st));
+  PP_TRY(pp::launch_qc_build(Q, n, p, w.Pim, w.Bre, w.Bim, st));
+  const int64_t plm = p * l * m;
+  int np_r = 0, np_i = 0, np_a = 0;
+  // Re: M(t, s) = Re Q(s, t) = Q[2 (s p + t)]
+  PP_TRY(pp::launch_mode3_tc(Q, 2, 2 * p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_r, w.part_a,
+                             &np_a, w.part_h, w.status, st));
+  PP_TRY(pp::launch_mode3_tc(w.Pim, n, 1, A, w.Ah + plm, p, n, l * m, nullptr, nullptr, &np_i,
+                             nullptr, nullptr, w.part_h + np_r, w.status, st));
+  PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
+  PP_TRY(pp::launch_sum_partials(w.part_h, np_r + np_i, w.scal + 1, st));
+  pp::CJacobiArgs ja;
+  ja.Xre = w.Ah;
+  ja.Xim = w.Ah + plm;
+  ja.W = w.W;
+  ja.sig = w.sig;
+  ja.perm = w.perm;
+  ja.sweeps = w.sweeps;
+  ja.status = w.status;
+  ja.l = l;
+  ja.m = m;
+  ja.p = p;
+  ja.a_pad = (int)pp::cjacobi_apad(l, m);
+  ja.max_sweeps = o.max_sweeps;
+  ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(l, m);
+  PP_TRY(pp::launch_cjacobi(ja, st));
+  return PP_OK;
+}
+
+// A_k = A-hat_k x_3 Q: Re = [Re Q | -Im Q] [Re; Im], Im = [Im Q | Re Q] [Re; Im];
+// err2 (scal[2]) = |A - Re A_k|^2 + |Im A_k|^2
+pp_status cbackproject(const float *A, int64_t l, int64_t m, int64_t n, int64_t p,
+                       const float *Xhat, float *Yre, float *Yim, const CDecompWs &w,
+                       double *err_out, cudaStream_t st) {
+  int np1 = 0, np2 = 0;
+  PP_TRY(pp::launch_mode3_tc(w.Bre, 2 * p, 1, Xhat, Yre, n, 2 * p, l * m, A, w.part_e, &np1,
+                             nullptr, nullptr, nullptr, w.status, st));
+  PP_TRY(pp::launch_mode3_tc(w.Bim, 2 * p, 1, Xhat, Yim, n, 2 * p, l * m, nullptr, nullptr, &np2,
+                             nullptr, nullptr, w.part_e + np1, w.status, st));
+  if (err_out) PP_TRY(pp::launch_sum_partials(w.part_e, np1 + np2, err_out, st));
+  return PP_OK;
+}
+
+pp::CFactorArgs cfactor_args(const CDecompWs &w, int64_t l, int64_t m, int64_t p) {
+  pp::CFactorArgs fa{};
+  fa.Xre = w.Ah;
+  fa.Xim = w.Ah + p * l * m;
+  fa.W = w.W;
+  fa.sig = w.sig;
+  fa.perm = w.perm;
+  fa.l = l;
+  fa.m = m;
+  fa.p = p;
+  fa.b = l < m ? l : m;
+  fa.a_pad = pp::cjacobi_apad(l, m);
+  fa.Ahk = w.Ahk;
+  return fa;
+}
+
 bool bad_dims(int64_t l, int64_t m, int64_t n, int64_t p) {
   return l < 1 || m < 1 || n < 1 || p < 1 || p > n || l > (1 << 20) || m > (1 << 20) ||
          n > (1 << 20) || l * m > (int64_t)1 << 31;
@@ -383,6 +488,21 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
           bad_dims(sh->l, sh->n2, sh->n, sh->p))
         return 0;
       carve_bwd(c, sh->l, sh->m, sh->n2, sh->n, sh->p);
+      return c.off;
+    case PP_OP_PPROD_C:
+      if (sh->l < 1 || sh->m < 1 || sh->n2 < 1 || bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
+      c.take<float>(sh->p * sh->n);
+      c.take<float>(2 * sh->n * sh->p);
+      c.take<float>(2 * sh->n * sh->p);
+      c.take<float>(2 * sh->p * sh->l * sh->m);
+      c.take<float>(2 * sh->p * sh->m * sh->n2);
+      c.take<float>(2 * sh->p * sh->l * sh->n2);
+      c.take<int32_t>(1);
+      return c.off;
+    case PP_OP_TSVDQ_C:
+    case PP_OP_TSVDQII_C:
+      if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
+      carve_cdecomp(c, sh->l, sh->m, sh->n, sh->p, op == PP_OP_TSVDQII_C);
       return c.off;
     case PP_OP_U3:
       if (bad_dims(sh->l, sh->m, sh->n, sh->p)) return 0;
@@ -826,6 +946,146 @@ pp_status pp_hosvd_matched_k2(int64_t l, int64_t m, int64_t n, int64_t p, int64_
     if (r > cap) r = cap;
   }
   *k2 = r < 1 ? 0 : r;
+  return PP_OK;
+}
+
+pp_status pprod_c(const float *A, const float *B, const float *Q, int64_t n1, int64_t m,
+                  int64_t n2, int64_t n, int64_t p, float *C_re, float *C_im, void *ws,
+                  size_t ws_bytes, void *stream) {
+  if (!A || !B || !Q || !C_re || !C_im) return PP_EINVAL;
+  if (bad_dims(n1, m, n, p) || bad_dims(m, n2, n, p) || bad_dims(n1, n2, n, p)) return PP_ESHAPE;
+  pp_shape sh{n1, m, n, p, 0, n2};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_PPROD_C, &sh))) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  CDecompWs w{};
+  w.Pim = c.take<float>(p * n);
+  w.Bre = c.take<float>(2 * n * p);
+  w.Bim = c.take<float>(2 * n * p);
+  float *Ah = c.take<float>(2 * p * n1 * m);
+  float *Bh = c.take<float>(2 * p * m * n2);
+  float *Ch = c.take<float>(2 * p * n1 * n2);
+  w.status = c.take<int32_t>(1);
+  PP_TRY(pp::launch_qc_build(Q, n, p, w.Pim, w.Bre, w.Bim, st));
+  auto fwd = [&](const float *X, int64_t pix, float *Y) -> cudaError_t {   // X x_3 Q^H
+    cudaError_t e = pp::launch_mode3_tc(Q, 2, 2 * p, X, Y, p, n, pix, nullptr, nullptr, nullptr,
+                                        nullptr, nullptr, nullptr, nullptr, st);
+    if (e != cudaSuccess) return e;
+    return pp::launch_mode3_tc(w.Pim, n, 1, X, Y + p * pix, p, n, pix, nullptr, nullptr, nullptr,
+                               nullptr, nullptr, nullptr, nullptr, st);
+  };
+  PP_TRY(fwd(A, n1 * m, Ah));
+  PP_TRY(fwd(B, m * n2, Bh));
+  PP_TRY(pp::launch_cfacewise(Ah, Bh, Ch, n1, m, n2, p, st));
+  PP_TRY(pp::launch_mode3_tc(w.Bre, 2 * p, 1, Ch, C_re, n, 2 * p, n1 * n2, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, nullptr, st));
+  PP_TRY(pp::launch_mode3_tc(w.Bim, 2 * p, 1, Ch, C_im, n, 2 * p, n1 * n2, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, nullptr, nullptr, st));
+  return PP_OK;
+}
+
+pp_status tsvdq_trunc_c(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
+                        int64_t p, int64_t k, float *Uh, float *s, float *Vh, float *Ak_re,
+                        float *Ak_im, pp_report *rep, const pp_opts *opts, void *ws,
+                        size_t ws_bytes, void *stream) {
+  if (!A || !Q || !Uh || !s || !Vh || ((Ak_re == nullptr) != (Ak_im == nullptr)))
+    return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  const int64_t b = l < m ? l : m;
+  if (k < 1 || k > b) return PP_ESHAPE;
+  if (pp::cjacobi_smem(l, m) > CJ_SMEM_BUDGET) return PP_ENOSYS;
+  pp_shape sh{l, m, n, p, k, 0};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_TSVDQ_C, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const CDecompWs w = carve_cdecomp(c, l, m, n, p, false);
+  if (pp_status e = cproject_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  pp::CFactorArgs fa = cfactor_args(w, l, m, p);
+  fa.kfix = k;
+  fa.Uh = reinterpret_cast<float2 *>(Uh);
+  fa.Vh = reinterpret_cast<float2 *>(Vh);
+  fa.s = s;
+  fa.kept_partial = w.kept_p;
+  fa.disc_partial = w.disc_p;
+  PP_TRY(pp::launch_cfactors(fa, st));
+  if (pp_status e = cbackproject(A, l, m, n, p, w.Ahk, Ak_re, Ak_im, w, w.scal + 2, st)) return e;
+  if (rep) {
+    pp::ReportArgs ra;
+    ra.rep = rep;
+    ra.status = w.status;
+    ra.sweeps = w.sweeps;
+    ra.p = p;
+    ra.normA2 = w.scal + 0;
+    ra.normAh2 = w.scal + 1;
+    ra.err2 = w.scal + 2;
+    ra.kept_partial = w.kept_p;
+    ra.disc_partial = w.disc_p;
+    ra.sel_scal = nullptr;
+    ra.K = nullptr;
+    ra.kappa_fixed = k * p;
+    ra.offs = nullptr;
+    PP_TRY(pp::launch_report(ra, st));
+  }
+  return PP_OK;
+}
+
+pp_status tsvdqII_c(const float *A, const float *Q, int64_t l, int64_t m, int64_t n, int64_t p,
+                    double gamma, int32_t *rho, int64_t *offs, float *Uh_pk, float *s_pk,
+                    float *Vh_pk, float *Ak_re, float *Ak_im, pp_report *rep,
+                    const pp_opts *opts, void *ws, size_t ws_bytes, void *stream) {
+  if (!A || !Q || !rho || !offs || !Uh_pk || !s_pk || !Vh_pk ||
+      ((Ak_re == nullptr) != (Ak_im == nullptr)))
+    return PP_EINVAL;
+  if (!(gamma > 0.0 && gamma <= 1.0)) return PP_EINVAL;
+  if (bad_dims(l, m, n, p)) return PP_ESHAPE;
+  if (pp::cjacobi_smem(l, m) > CJ_SMEM_BUDGET) return PP_ENOSYS;
+  pp_shape sh{l, m, n, p, 0, 0};
+  if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_TSVDQII_C, &sh))) return e;
+  const Opts o = read_opts(opts);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Carve c(ws);
+  const CDecompWs w = carve_cdecomp(c, l, m, n, p, true);
+  const int64_t b = l < m ? l : m;
+  if (pp_status e = cproject_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  pp::SelectArgs sa;
+  sa.sig = w.sig;
+  sa.p = p;
+  sa.b = b;
+  sa.gamma = gamma;
+  sa.keys_sorted = w.keys;
+  sa.rank = w.rank;
+  sa.rho = rho;
+  sa.offs = offs;
+  sa.scal = w.scal + 4;
+  sa.K = w.K;
+  PP_TRY(pp::launch_select(sa, st));
+  pp::CFactorArgs fa = cfactor_args(w, l, m, p);
+  fa.kfix = 0;
+  fa.rho = rho;
+  fa.offs = offs;
+  fa.Uh = reinterpret_cast<float2 *>(Uh_pk);
+  fa.Vh = reinterpret_cast<float2 *>(Vh_pk);
+  fa.s = s_pk;
+  PP_TRY(pp::launch_cfactors(fa, st));
+  if (pp_status e = cbackproject(A, l, m, n, p, w.Ahk, Ak_re, Ak_im, w, w.scal + 2, st)) return e;
+  if (rep) {
+    pp::ReportArgs ra;
+    ra.rep = rep;
+    ra.status = w.status;
+    ra.sweeps = w.sweeps;
+    ra.p = p;
+    ra.normA2 = w.scal + 0;
+    ra.normAh2 = w.scal + 1;
+    ra.err2 = w.scal + 2;
+    ra.kept_partial = nullptr;
+    ra.disc_partial = nullptr;
+    ra.sel_scal = w.scal + 4;
+    ra.K = w.K;
+    ra.kappa_fixed = -1;
+    ra.offs = offs;
+    PP_TRY(pp::launch_report(ra, st));
+  }
   return PP_OK;
 }
 

@@ -131,6 +131,47 @@ struct FactorArgs {
 };
 cudaError_t launch_factors(const FactorArgs &a, cudaStream_t st);
 
+// ---------------------------------------------------------------- complex Q (pp_complex.cu)
+// Real matrices from a complex Q (n x p, interleaved): Pim (p x n) = -Im(Q)^T,
+// Bre (n x 2p) = [Re Q | -Im Q], Bim (n x 2p) = [Im Q | Re Q].
+cudaError_t launch_qc_build(const float *Qf, int64_t n, int64_t p, float *Pim, float *Bre,
+                            float *Bim, cudaStream_t st);
+// PP_ENOTORTHO into *status when some |(Q^H Q - I)(i, j)| > tol
+cudaError_t launch_qc_check(const float *Qf, int64_t n, int64_t p, float tol, int32_t *status,
+                            cudaStream_t st);
+struct CJacobiArgs {
+  const float *Xre, *Xim;     // p complex slices l x m, planar
+  float2 *W;                  // p * b * a_pad converged vectors
+  float *sig;                 // p * b, descending per slice
+  int32_t *perm;              // p * b: sorted position -> vector index
+  int32_t *sweeps;            // p
+  int32_t *status;
+  int64_t l, m, p;
+  int a_pad;                  // cjacobi_apad(l, m)
+  int32_t max_sweeps;
+  float tol;
+};
+int64_t cjacobi_apad(int64_t l, int64_t m);
+size_t cjacobi_smem(int64_t l, int64_t m);   // the slice must fit one CTA's shared memory
+cudaError_t launch_cjacobi(const CJacobiArgs &a, cudaStream_t st);
+struct CFactorArgs {
+  const float *Xre, *Xim;     // A-hat, planar
+  const float2 *W;
+  const float *sig;
+  const int32_t *perm;
+  int64_t l, m, p, b, a_pad;
+  int64_t kfix;               // fixed rank, or 0 -> ragged from rho / offs
+  const int32_t *rho;
+  const int64_t *offs;
+  float2 *Uh, *Vh;            // complex factors (interleaved), layouts as the real ones
+  float *s;
+  float *Ahk;                 // rebuilt transform domain, planar stacked (2 p l m), or nullptr
+  double *kept_partial, *disc_partial;
+};
+cudaError_t launch_cfactors(const CFactorArgs &a, cudaStream_t st);
+// C_t = A_t B_t (complex, planar stacked operands: p real slices then p imaginary)
+cudaError_t launch_cfacewise(const float *A, const float *B, float *C, int64_t n1, int64_t m,
+                             int64_t n2, int64_t p, cudaStream_t st);
 // ---------------------------------------------------------------- reductions
 // partials[blk] = sum of x^2 over a fixed grid; returns the number of partials.
 cudaError_t launch_sumsq(const float *x, int64_t n, double *partials, int *n_partials,

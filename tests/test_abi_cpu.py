@@ -154,3 +154,26 @@ def test_u3_builder_host_validation():
     assert L.pprod_u3(FAKE, 4, 4, 8, 9, FAKE, None, None, None, FAKE, 1 << 30, None) == b.PP_ESHAPE
     assert L.pprod_u3(FAKE, 4, 4, 1000, 9, FAKE, None, None, None, FAKE, 1 << 40, None) == b.PP_ENOSYS
     assert L.pprod_u3(FAKE, 4, 4, 8, 2, FAKE, None, None, None, FAKE, 16, None) == b.PP_EWORKSPACE
+
+
+def test_complex_entry_points_validate_on_host():
+    b = _lib()
+    L = b.lib()
+    o = b.pp_opts()
+    # mismatched A_k pointers, NULL factors, bad k, gamma, slice too large for the complex Jacobi
+    assert L.tsvdq_trunc_c(FAKE, FAKE, 4, 6, 8, 2, 2, FAKE, FAKE, FAKE, FAKE, None, None,
+                           ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_EINVAL
+    assert L.tsvdq_trunc_c(FAKE, FAKE, 4, 6, 8, 2, 2, None, FAKE, FAKE, None, None, None,
+                           ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_EINVAL
+    assert L.tsvdq_trunc_c(FAKE, FAKE, 4, 6, 8, 2, 5, FAKE, FAKE, FAKE, None, None, None,
+                           ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_ESHAPE
+    for g in (0.0, 1.5):
+        assert L.tsvdqII_c(FAKE, FAKE, 4, 6, 8, 2, g, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                           None, ctypes.byref(o), FAKE, 1 << 30, None) == b.PP_EINVAL
+    assert L.tsvdqII_c(FAKE, FAKE, 400, 400, 8, 2, 0.9, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                       None, ctypes.byref(o), FAKE, 1 << 40, None) == b.PP_ENOSYS
+    assert L.tsvdqII_c(FAKE, FAKE, 4, 6, 8, 2, 0.9, FAKE, FAKE, FAKE, FAKE, FAKE, None, None,
+                       None, ctypes.byref(o), FAKE, 16, None) == b.PP_EWORKSPACE
+    assert L.pprod_c(FAKE, FAKE, FAKE, 3, 3, 3, 4, 5, FAKE, FAKE, FAKE, 1 << 20, None) == b.PP_ESHAPE
+    assert b.workspace_bytes(b.PP_OP_TSVDQII_C, l=120, m=160, n=300, p=50) > \
+        2 * b.workspace_bytes(b.PP_OP_PPROD_C, l=4, m=4, n=8, p=2, n2=4)
