@@ -320,22 +320,29 @@ __device__ __forceinline__ float group_sum_smem(float v, float *wred, unsigned m
 // symmetric Schur rotation that zeroes g; t is its tangent.
 __device__ __forceinline__ void pair_angle(float g, float al, float be, float &t, float &s,
                                            float &tau) {
-  // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (be - al) / (2 g), written
-  // without zeta: t = sign(d) 2g / (|d| + sqrt(d^2 + 4 g^2)), d = be - al
+  // With d = be - al and h = sqrt(d^2 + 4 g^2) (1/h from rsqrt refined by one
+  // Newton step): the rotation angle theta has cos(2 theta) = |d| / h, so
+  // cos^2(theta) = (h + |d|) / (2h) and t = tan(theta) = sign(d) 2g / (h + |d|)
+  // (the symmetric Schur tangent).  c and 1/(h + |d|) come from two
+  // independent MUFU operations, each refined by one Newton step; then
+  // tau = s / (1 + c) (Rutishauser: implied cosine 1 - s tau), also refined.
   const float d = be - al, g2x = 2.f * g;
   const float r = fmaf(d, d, g2x * g2x);
-  const float h = r * rsqrtf(r);
-  t = copysignf(1.f, d) * __fdividef(g2x, fabsf(d) + h);
-  const float u = fmaf(t, t, 1.f);
-  float c = rsqrtf(u);
-  c = c * fmaf(-0.5f * u * c, c, 1.5f);          // one Newton step: c = 1/sqrt(1 + t^2)
+  float ih = rsqrtf(r);
+  ih = ih * fmaf(-0.5f * r * ih, ih, 1.5f);
+  const float q = fmaf(r, ih, fabsf(d));          // h + |d|, in [h, 2h]
+  const float c2 = 0.5f * q * ih;                 // cos^2(theta), in [1/2, 1]
+  float rc = rsqrtf(c2);
+  float iq = __fdividef(1.f, q);
+  rc = rc * fmaf(-0.5f * c2 * rc, rc, 1.5f);
+  iq = fmaf(iq, fmaf(-q, iq, 1.f), iq);
+  const float c = c2 * rc;
+  t = copysignf(1.f, d) * g2x * iq;
   s = c * t;
-  // tau = s / (1 + c) (Rutishauser: implied cosine 1 - s tau), reciprocal refined
-  // by one Newton step so that tau is accurate to about half an ulp
-  const float onec = 1.f + c;                    // in [1, 2]: no special cases
-  float rc = __fdividef(1.f, onec);
-  rc = fmaf(rc, fmaf(-onec, rc, 1.f), rc);
-  tau = s * rc;
+  const float onec = 1.f + c;                     // in [1.7, 2]: no special cases
+  float rp = __fdividef(1.f, onec);
+  rp = fmaf(rp, fmaf(-onec, rp, 1.f), rp);
+  tau = s * rp;
 }
 
 __device__ __forceinline__ void rotate4(float4 &x, float4 &y, float s, float tau) {

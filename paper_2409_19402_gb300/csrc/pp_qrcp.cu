@@ -39,7 +39,7 @@ __host__ __device__ inline int64_t qr_smem_floats(int64_t b, int64_t a) {
   return b * qr_ap(a) + 3 * b;               // vectors, diagonal, used flags, order
 }
 
-constexpr int QR_NREG = 12;                  // float4 per lane held in registers in the update
+constexpr int QR_NREG = 11;                  // float4 per lane held in registers in the update
 
 // y -= f h on a float4; the squared entries above k join the trailing norm
 // (four partial sums; masked only in the float4 that holds entry k)
@@ -84,6 +84,42 @@ __device__ __forceinline__ float4 qr_h4(const float4 *p4, int e4, int k4, int k,
     h.w = e + 3 < k ? 0.f : (e + 3 == k ? vk : h.w);
   }
   return h;
+}
+
+// The reflector applied to one vector held in registers: NQ float4 per lane
+// (the last one guarded), one read and one write of the vector; the squared
+// entries above k accumulate in s4.  Instantiated for NQ = 1..QR_NREG so that
+// late steps, whose vectors are short, issue only their live chunks.
+template <int NQ>
+__device__ __forceinline__ void qr_update_regs(float4 *y4, const float4 *p4, int k4, int k,
+                                               float vk, float beta, int glane, unsigned gmask,
+                                               int ap4, float4 &s4) {
+  float4 r[NQ];
+  float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e4 = k4 + glane + QG * q;
+    if (q < NQ - 1 || e4 < ap4) {
+      r[q] = y4[e4];
+      const float4 h = qr_h4(p4, e4, k4, k, vk);
+      c4.x = fmaf(h.x, r[q].x, c4.x);
+      c4.y = fmaf(h.y, r[q].y, c4.y);
+      c4.z = fmaf(h.z, r[q].z, c4.z);
+      c4.w = fmaf(h.w, r[q].w, c4.w);
+    }
+  }
+  float c = (c4.x + c4.y) + (c4.z + c4.w);
+#pragma unroll
+  for (int o = QG / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, QG);
+  const float fct = beta * c;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e4 = k4 + glane + QG * q;
+    if (q < NQ - 1 || e4 < ap4) {
+      qr_update4(r[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
+      y4[e4] = r[q];
+    }
+  }
 }
 
 __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
@@ -170,6 +206,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
       order[k] = sp;
     }
     const bool in_regs = ap4 - k4 <= QG * QR_NREG;
+    const int nq = (ap4 - k4 + QG - 1) / QG;
     float bestv = 0.f;
     unsigned bestj = QR_NONE;
     for (int j = grp; j < b; j += ngrp) {
@@ -177,30 +214,15 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
       float4 *y4 = reinterpret_cast<float4 *>(Y + (size_t)j * ap);
       float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f), s4 = c4;
       if (in_regs) {                           // one read and one write of the vector
-        float4 r[QR_NREG];
-#pragma unroll
-        for (int q = 0; q < QR_NREG; ++q) {
-          const int e4 = k4 + glane + QG * q;
-          if (e4 < ap4) {
-            r[q] = y4[e4];
-            const float4 h = qr_h4(p4, e4, k4, k, vk);
-            c4.x = fmaf(h.x, r[q].x, c4.x);
-            c4.y = fmaf(h.y, r[q].y, c4.y);
-            c4.z = fmaf(h.z, r[q].z, c4.z);
-            c4.w = fmaf(h.w, r[q].w, c4.w);
-          }
-        }
-        float c = (c4.x + c4.y) + (c4.z + c4.w);
-#pragma unroll
-        for (int o = QG / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, QG);
-        const float fct = beta * c;
-#pragma unroll
-        for (int q = 0; q < QR_NREG; ++q) {
-          const int e4 = k4 + glane + QG * q;
-          if (e4 < ap4) {
-            qr_update4(r[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
-            y4[e4] = r[q];
-          }
+        switch (nq) {                          // live float4 per lane, uniform in the CTA
+#define QR_CASE(NQ) \
+  case NQ:          \
+    qr_update_regs<NQ>(y4, p4, k4, k, vk, beta, glane, gmask, ap4, s4); \
+    break;
+          QR_CASE(1) QR_CASE(2) QR_CASE(3) QR_CASE(4) QR_CASE(5) QR_CASE(6)
+          QR_CASE(7) QR_CASE(8) QR_CASE(9) QR_CASE(10) QR_CASE(11)
+#undef QR_CASE
+          default: break;
         }
       } else {                                 // long vectors: a read pass, then read-write
         for (int e4 = k4 + glane; e4 < ap4; e4 += QG) {
