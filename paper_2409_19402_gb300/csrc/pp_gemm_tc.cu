@@ -16,8 +16,9 @@
 //
 // Operands: the tensor is pixel-contiguous, i.e. MN-major for this product,
 // and M is tiny; both are streamed by the 128 threads of the CTA in chunks of
-// 32 along S and written into shared memory in the K-major, 128-byte-swizzled
-// canonical layout (row = pixel or slice, 32 tf32 = 128 bytes per row, 8-row
+// 32 along S (each thread's values for chunk c + 1 are requested while chunk c
+// is written and issued) and written into shared memory in the K-major,
+// 128-byte-swizzled canonical layout (row = pixel or slice, 32 tf32 = 128 bytes per row, 8-row
 // atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  Each load of a
 // warp covers 32 consecutive pixels (coalesced).  Two
 // stages: while the MMAs of chunk c run, the threads fill chunk c+1; a stage
@@ -181,6 +182,21 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
   const int nchunks = (int)((S + TK - 1) / TK);
   double xs = 0.0;
   bool ok = true;
+  // chunk c's operands are loaded into registers one iteration ahead, so the
+  // global-memory latency overlaps the previous chunk's barrier and MMA issue
+  const int64_t pix = n0 + row;
+  const int64_t trow = y0 + row;
+  float va[TK / 2], vb[TK / 2];
+  auto load_chunk = [&](int c) {
+    const int64_t s0 = (int64_t)c * TK;
+#pragma unroll
+    for (int k = 0; k < TK / 2; ++k) {
+      const int64_t s = s0 + khalf * (TK / 2) + k;
+      va[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
+      vb[k] = (row < NT && trow < P && s < S) ? Qm[trow * sr + s * sc] : 0.f;
+    }
+  };
+  if (nchunks > 0) load_chunk(0);
   for (int c = 0; c < nchunks; ++c) {
     const int st = c & 1;   // smem stage and TMEM buffer
     unsigned char *base = smem + st * STAGE;
@@ -190,57 +206,43 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
       asm volatile("tcgen05.fence::after_thread_sync;");
       tmem_accumulate(tmem, st, warp, acc);
     }
-    const int64_t s0 = (int64_t)c * TK;
     // ---- A: pixel row `row`, 16 values along S (this thread's half of the chunk)
     {
-      float v[TK / 2];
-      const int64_t pix = n0 + row;
-#pragma unroll
-      for (int k = 0; k < TK / 2; ++k) {
-        const int64_t s = s0 + khalf * (TK / 2) + k;
-        v[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
-      }
       unsigned char *ah = base, *al = base + A_BYTES;
       float xq = 0.f;
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
         const int ch = khalf * 4 + c4;
         float4 h, l;
-        h.x = tf32_rna(v[4 * c4 + 0]); l.x = tf32_rna(v[4 * c4 + 0] - h.x);
-        h.y = tf32_rna(v[4 * c4 + 1]); l.y = tf32_rna(v[4 * c4 + 1] - h.y);
-        h.z = tf32_rna(v[4 * c4 + 2]); l.z = tf32_rna(v[4 * c4 + 2] - h.z);
-        h.w = tf32_rna(v[4 * c4 + 3]); l.w = tf32_rna(v[4 * c4 + 3] - h.w);
+        h.x = tf32_rna(va[4 * c4 + 0]); l.x = tf32_rna(va[4 * c4 + 0] - h.x);
+        h.y = tf32_rna(va[4 * c4 + 1]); l.y = tf32_rna(va[4 * c4 + 1] - h.y);
+        h.z = tf32_rna(va[4 * c4 + 2]); l.z = tf32_rna(va[4 * c4 + 2] - h.z);
+        h.w = tf32_rna(va[4 * c4 + 3]); l.w = tf32_rna(va[4 * c4 + 3] - h.w);
         const uint32_t off = sw128_chunk(row, ch);
         *reinterpret_cast<float4 *>(ah + off) = h;
         *reinterpret_cast<float4 *>(al + off) = l;
-        xq = fmaf(v[4 * c4], v[4 * c4], fmaf(v[4 * c4 + 1], v[4 * c4 + 1],
-             fmaf(v[4 * c4 + 2], v[4 * c4 + 2], fmaf(v[4 * c4 + 3], v[4 * c4 + 3], xq))));
+        xq = fmaf(va[4 * c4], va[4 * c4], fmaf(va[4 * c4 + 1], va[4 * c4 + 1],
+             fmaf(va[4 * c4 + 2], va[4 * c4 + 2], fmaf(va[4 * c4 + 3], va[4 * c4 + 3], xq))));
       }
       if (do_x) xs += (double)xq;   // FP32 over 16 values, FP64 across chunks
     }
     // ---- B: output-slice row `row` (< NT), 16 values along S: M(y0 + row, s0 + k)
     if (row < NT) {
-      float v[TK / 2];
-      const int64_t t = y0 + row;
-#pragma unroll
-      for (int k = 0; k < TK / 2; ++k) {
-        const int64_t s = s0 + khalf * (TK / 2) + k;
-        v[k] = (t < P && s < S) ? Qm[t * sr + s * sc] : 0.f;
-      }
       unsigned char *bh = base + 2 * A_BYTES, *bl = bh + B_BYTES;
 #pragma unroll
       for (int c4 = 0; c4 < 4; ++c4) {
         const int ch = khalf * 4 + c4;
         float4 h, l;
-        h.x = tf32_rna(v[4 * c4 + 0]); l.x = tf32_rna(v[4 * c4 + 0] - h.x);
-        h.y = tf32_rna(v[4 * c4 + 1]); l.y = tf32_rna(v[4 * c4 + 1] - h.y);
-        h.z = tf32_rna(v[4 * c4 + 2]); l.z = tf32_rna(v[4 * c4 + 2] - h.z);
-        h.w = tf32_rna(v[4 * c4 + 3]); l.w = tf32_rna(v[4 * c4 + 3] - h.w);
+        h.x = tf32_rna(vb[4 * c4 + 0]); l.x = tf32_rna(vb[4 * c4 + 0] - h.x);
+        h.y = tf32_rna(vb[4 * c4 + 1]); l.y = tf32_rna(vb[4 * c4 + 1] - h.y);
+        h.z = tf32_rna(vb[4 * c4 + 2]); l.z = tf32_rna(vb[4 * c4 + 2] - h.z);
+        h.w = tf32_rna(vb[4 * c4 + 3]); l.w = tf32_rna(vb[4 * c4 + 3] - h.w);
         const uint32_t off = sw128_chunk(row, ch);
         *reinterpret_cast<float4 *>(bh + off) = h;
         *reinterpret_cast<float4 *>(bl + off) = l;
       }
     }
+    if (c + 1 < nchunks) load_chunk(c + 1);   // next chunk's loads in flight
     // generic-proxy writes -> visible to the tensor core (async proxy); the
     // TMEM reads above are ordered before the MMAs that overwrite the buffer
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
