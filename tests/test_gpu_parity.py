@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded FP32 inputs.
 
-Tolerances (stated per spec requirement of the method's accuracy):
+Tolerances (what the accuracy of the method's FP32 results supports):
   * mode-3 products (tensor cores, 3-pass split TF32): per entry
     |y~ - y| <= (2 S + 16) u sum_s |M(t,s)| |X(s)|, u = 2^-24, S terms: the
     split drops at most 3 * 2^-22 = 12 u of each product, and S u per sum is
