@@ -518,13 +518,24 @@ def run_batched(args, torch, binding, stream, dev):
 
 
 def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
-    """Same metric through host buffers: pinned A, Q copied in and the compressed
-    representation (report, rho, offs, packed factors) copied out every step."""
+    """Same metric through host buffers: every step copies its inputs (A, Q) in
+    from pinned host memory and its compressed representation (report, rho,
+    offs, the packed factors) out to pinned host memory.  Two buffer sets and
+    a copy stream pipeline the steps, as a streaming user would: step i's
+    inputs go in while step i-1 computes and step i-2's result comes out.
+    The serial variant (each step copies in, computes and copies out before
+    the next begins) is reported beside it."""
     A_h = torch.from_numpy(A).pin_memory()
     Q_h = torch.from_numpy(Qp).pin_memory()
-    e2e_times = []
-    d2h_bytes = []
-    for i in range(args.warmup + args.steps):
+    n_steps = args.warmup + args.steps
+
+    def d2h_bytes(kappa):
+        return (binding.REPORT_BYTES + run.rho.numel() * 4 + run.offs.numel() * 8 +
+                4 * kappa * (L + M + 1))
+
+    # ---- serial
+    serial = []
+    for i in range(n_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
@@ -533,29 +544,84 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
             run(stream)
             hdr = torch.empty(binding.REPORT_BYTES, dtype=torch.uint8).pin_memory()
             hdr.copy_(run.rep, non_blocking=True)
-            rho_h = run.rho.to("cpu", non_blocking=True)
             offs_h = run.offs.to("cpu", non_blocking=True)
         stream.synchronize()
         kappa = int(offs_h[-1])
         with torch.cuda.stream(stream):
-            U_h = run.Uh[:kappa * L].to("cpu", non_blocking=True)
-            s_h = run.s[:kappa].to("cpu", non_blocking=True)
-            V_h = run.Vh[:kappa * M].to("cpu", non_blocking=True)
+            run.Uh[:kappa * L].to("cpu", non_blocking=True)
+            run.s[:kappa].to("cpu", non_blocking=True)
+            run.Vh[:kappa * M].to("cpu", non_blocking=True)
         stream.synchronize()
-        dt = time.perf_counter() - t0
         if i >= args.warmup:
-            e2e_times.append(dt)
-            d2h_bytes.append(binding.REPORT_BYTES + rho_h.numel() * 4 + offs_h.numel() * 8 +
-                             4 * (U_h.numel() + s_h.numel() + V_h.numel()))
-    e2e_s = sum(e2e_times)
+            serial.append(time.perf_counter() - t0)
+    serial_s = sum(serial)
+
+    # ---- pipelined: two buffer sets, copies on their own stream
+    runs = [run, Runner(torch.empty_like(run.A), torch.empty_like(run.Q), run.gamma, torch,
+                        binding, precond=run.opts.precond >= 0)]
+    cps = torch.cuda.Stream(device=dev)
+    h2d_done = [torch.cuda.Event(), torch.cuda.Event()]
+    comp_done = [torch.cuda.Event(), torch.cuda.Event()]
+    out_done = [torch.cuda.Event(), torch.cuda.Event()]
+    small = [(torch.empty(binding.REPORT_BYTES, dtype=torch.uint8).pin_memory(),
+              torch.empty(run.offs.numel(), dtype=torch.int64).pin_memory(),
+              torch.empty(run.rho.numel(), dtype=torch.int32).pin_memory()) for _ in range(2)]
+    cap = run.s.numel()
+    big = [(torch.empty(cap * L, dtype=torch.float32).pin_memory(),
+            torch.empty(cap, dtype=torch.float32).pin_memory(),
+            torch.empty(cap * M, dtype=torch.float32).pin_memory()) for _ in range(2)]
+    moved = []
+    torch.cuda.synchronize()
+
+    def finish(j):                      # step j's result out (after its compute)
+        bj = j % 2
+        comp_done[bj].synchronize()
+        kappa = int(small[bj][1][-1])
+        r = runs[bj]
+        with torch.cuda.stream(cps):
+            big[bj][0][:kappa * L].copy_(r.Uh[:kappa * L], non_blocking=True)
+            big[bj][1][:kappa].copy_(r.s[:kappa], non_blocking=True)
+            big[bj][2][:kappa * M].copy_(r.Vh[:kappa * M], non_blocking=True)
+            out_done[bj].record(cps)
+        moved.append(d2h_bytes(kappa))
+
+    t0 = None
+    for i in range(n_steps):
+        if i == args.warmup:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            moved.clear()
+        bi = i % 2
+        r = runs[bi]
+        with torch.cuda.stream(cps):                # inputs in (buffer free once step i-2 left)
+            if i >= 2:
+                cps.wait_event(out_done[bi])
+            r.A.copy_(A_h, non_blocking=True)
+            r.Q.copy_(Q_h, non_blocking=True)
+            h2d_done[bi].record(cps)
+        with torch.cuda.stream(stream):
+            stream.wait_event(h2d_done[bi])
+            r(stream)
+            small[bi][0].copy_(r.rep, non_blocking=True)
+            small[bi][1].copy_(r.offs, non_blocking=True)
+            small[bi][2].copy_(r.rho, non_blocking=True)
+            comp_done[bi].record(stream)
+        if i >= 1:
+            finish(i - 1)
+    finish(n_steps - 1)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
     if dist is not None:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        t = torch.tensor([e2e_s, serial_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+        e2e_s, serial_s = float(t[0].item()), float(t[1].item())
     return {"value": world * L * M * N * args.steps / e2e_s, "unit": UNIT,
             "h2d_bytes_per_step": int(A.nbytes + Qp.nbytes),
-            "d2h_bytes_per_step": int(statistics.mean(d2h_bytes)),
-            "ms_per_step": 1e3 * e2e_s / args.steps}
+            "d2h_bytes_per_step": int(statistics.mean(moved[:args.steps])),
+            "ms_per_step": 1e3 * e2e_s / args.steps,
+            "pipelined": "two buffer sets; inputs in on a copy stream while the previous step computes",
+            "serial": {"value": world * L * M * N * args.steps / serial_s,
+                       "ms_per_step": 1e3 * serial_s / args.steps}}
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
