@@ -52,7 +52,7 @@ __global__ void qc_check_kernel(const float *__restrict__ Qf, int64_t n, int64_t
 }
 
 // ------------------------------------------------------------ complex one-sided Jacobi
-constexpr int CJ_THREADS = 256;
+constexpr int CJ_THREADS = 1024;
 constexpr int CJ_G = 16;                       // lanes per pair
 
 __device__ __forceinline__ void cj_circle_pair(int N, int r, int slot, int &j, int &k) {
@@ -73,39 +73,78 @@ __device__ __forceinline__ float cj_group_sum(float v, unsigned mask) {
   return v;
 }
 
+// The pair's (real, imaginary) inner-product partials summed over its CJ_G
+// lanes through the warp's 32 float2 of scratch, in a fixed order (bitwise the
+// same in every lane of the group).
+__device__ __forceinline__ float2 cj_group_sum2(float2 v, float2 *wred, unsigned mask) {
+  const int wl = threadIdx.x & 31;
+  wred[wl] = v;
+  __syncwarp(mask);
+  const float4 *rp = reinterpret_cast<const float4 *>(wred + (wl & ~(CJ_G - 1)));
+  float2 sv[CJ_G / 4];
+#pragma unroll
+  for (int k = 0; k < CJ_G / 4; ++k) {
+    const float4 a = rp[2 * k], b = rp[2 * k + 1];          // four float2
+    sv[k] = make_float2((a.x + a.z) + (b.x + b.z), (a.y + a.w) + (b.y + b.w));
+  }
+#pragma unroll
+  for (int w = CJ_G / 8; w > 0; w >>= 1)
+#pragma unroll
+    for (int k = 0; k < w; ++k) sv[k] = make_float2(sv[k].x + sv[k + w].x, sv[k].y + sv[k + w].y);
+  __syncwarp(mask);
+  return sv[0];
+}
+
 // One pair x, y (complex, length a_pad): with g = x^H y = |g| e^{i phi}, the
-// vector y e^{-i phi} has a real non-negative inner product |g| with x, and the
-// real symmetric Schur rotation of the real kernel (Rutishauser form
-// x' = x - s (y' + tau x), y'' = y' + s (x - tau y')) zeroes it; the phase
-// factor and the rotation together are unitary.  Squared norms are tracked.
+// unitary [[c, s e^{i phi}], [-s e^{-i phi}, c]] acting on [x y] gives
+// x'^H y' = e^{i phi} (c s (al - be) + (c^2 - s^2) |g|), zero for the real
+// symmetric Schur angle of (al, be, |g|); applied in Rutishauser's form
+// (1 - s tau = c).  Squared norms are tracked (al - t |g|, be + t |g|).  The
+// angle as in the real kernel: cos^2 = (h + |d|) / 2h, each MUFU result
+// refined by one Newton step.
 __device__ __forceinline__ bool cj_pair(float2 *__restrict__ x, float2 *__restrict__ y,
                                         float *na, float *nb, int a_pad, float tol2, int lane,
-                                        unsigned mask) {
+                                        unsigned mask, float2 *wred) {
   float gr = 0.f, gi = 0.f;
   for (int e = lane; e < a_pad; e += CJ_G) {
     const float2 u = x[e], v = y[e];
     gr = fmaf(u.x, v.x, fmaf(u.y, v.y, gr));
     gi = fmaf(u.x, v.y, fmaf(-u.y, v.x, gi));
   }
-  gr = cj_group_sum(gr, mask);
-  gi = cj_group_sum(gi, mask);
+  const float2 g = cj_group_sum2(make_float2(gr, gi), wred, mask);
   const float al = *na, be = *nb;
-  const float g2 = fmaf(gr, gr, gi * gi);
+  const float g2 = fmaf(g.x, g.x, g.y * g.y);
   if (g2 == 0.f || g2 <= tol2 * al * be) return false;
-  const float ag = sqrtf(g2);
-  const float cph = gr / ag, sph = gi / ag;      // e^{i phi}
+  float iag = rsqrtf(g2);
+  iag = iag * fmaf(-0.5f * g2 * iag, iag, 1.5f);
+  const float ag = g2 * iag;
+  const float cph = g.x * iag, sph = g.y * iag;   // e^{i phi}
   const float d = be - al, g2x = 2.f * ag;
   const float r = fmaf(d, d, g2x * g2x);
-  const float h = sqrtf(r);
-  const float t = copysignf(1.f, d) * (g2x / (fabsf(d) + h));
-  const float c = 1.f / sqrtf(fmaf(t, t, 1.f));
+  float ih = rsqrtf(r);
+  ih = ih * fmaf(-0.5f * r * ih, ih, 1.5f);
+  const float q = fmaf(r, ih, fabsf(d));          // h + |d|
+  const float c2 = 0.5f * q * ih;                 // cos^2(theta)
+  float rc = rsqrtf(c2);
+  float iq = __fdividef(1.f, q);
+  rc = rc * fmaf(-0.5f * c2 * rc, rc, 1.5f);
+  iq = fmaf(iq, fmaf(-q, iq, 1.f), iq);
+  const float c = c2 * rc;
+  const float t = copysignf(1.f, d) * g2x * iq;
   const float s = c * t;
-  const float tau = s / (1.f + c);
+  const float onec = 1.f + c;
+  float rp = __fdividef(1.f, onec);
+  rp = fmaf(rp, fmaf(-onec, rp, 1.f), rp);
+  const float tau = s * rp;
+  // x' = x - s (tau x + e^{-i phi} y),  y' = y + s (e^{i phi} x - tau y): the
+  // unitary [[c, s e^{i phi}], [-s e^{-i phi}, c]] (1 - s tau = c) with the phase
+  // only in the terms scaled by s, so its rounding moves no norm by more than s u
   for (int e = lane; e < a_pad; e += CJ_G) {
-    const float2 u = x[e], v0 = y[e];
-    const float2 v = make_float2(fmaf(v0.x, cph, v0.y * sph), fmaf(v0.y, cph, -v0.x * sph));
-    x[e] = make_float2(fmaf(-s, fmaf(tau, u.x, v.x), u.x), fmaf(-s, fmaf(tau, u.y, v.y), u.y));
-    y[e] = make_float2(fmaf(s, fmaf(-tau, v.x, u.x), v.x), fmaf(s, fmaf(-tau, v.y, u.y), v.y));
+    const float2 u = x[e], v = y[e];
+    const float2 pv = make_float2(fmaf(v.x, cph, v.y * sph), fmaf(v.y, cph, -v.x * sph));
+    const float2 pu = make_float2(fmaf(u.x, cph, -u.y * sph), fmaf(u.y, cph, u.x * sph));
+    x[e] = make_float2(fmaf(-s, fmaf(tau, u.x, pv.x), u.x), fmaf(-s, fmaf(tau, u.y, pv.y), u.y));
+    y[e] = make_float2(fmaf(s, fmaf(-tau, v.x, pu.x), v.x), fmaf(s, fmaf(-tau, v.y, pu.y), v.y));
   }
   if (lane == 0) {
     *na = fmaxf(fmaf(-t, ag, al), 0.f);
@@ -119,6 +158,8 @@ __device__ __forceinline__ bool cj_pair(float2 *__restrict__ x, float2 *__restri
 __global__ void __launch_bounds__(CJ_THREADS) cjacobi_kernel(CJacobiArgs A) {
   extern __shared__ __align__(16) float2 cw[];
   __shared__ int flag;
+  __shared__ __align__(16) float2 cj_red[CJ_THREADS];     // 32 float2 per warp
+  float2 *wred = cj_red + (threadIdx.x & ~31);
   const int64_t f = blockIdx.x;
   const int l = (int)A.l, m = (int)A.m;
   const bool rows = l <= m;
@@ -162,7 +203,7 @@ __global__ void __launch_bounds__(CJ_THREADS) cjacobi_kernel(CJacobiArgs A) {
         cj_circle_pair(N, r, slot, j, k);
         if (j >= b || k >= b) continue;
         if (cj_pair(cw + (size_t)j * ap, cw + (size_t)k * ap, nrm + j, nrm + k, ap, tol2, lane,
-                    mask) &&
+                    mask, wred) &&
             lane == 0)
           ++rot;
       }
