@@ -94,6 +94,9 @@ template <int NQ>
 __device__ __forceinline__ void qr_update_regs(float4 *y4, const float4 *p4, int k4, int k,
                                                float vk, float beta, int glane, unsigned gmask,
                                                int ap4, float4 &s4) {
+  // only chunk 0 of lane 0 (e4 == k4) holds entries at or below k; every other
+  // chunk starts at least 4 float4 past it and takes the plain path
+  const bool edge = glane == 0;
   float4 r[NQ];
   float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
@@ -101,7 +104,7 @@ __device__ __forceinline__ void qr_update_regs(float4 *y4, const float4 *p4, int
     const int e4 = k4 + glane + QG * q;
     if (q < NQ - 1 || e4 < ap4) {
       r[q] = y4[e4];
-      const float4 h = qr_h4(p4, e4, k4, k, vk);
+      const float4 h = (q == 0 && edge) ? qr_h4(p4, e4, k4, k, vk) : p4[e4];
       c4.x = fmaf(h.x, r[q].x, c4.x);
       c4.y = fmaf(h.y, r[q].y, c4.y);
       c4.z = fmaf(h.z, r[q].z, c4.z);
@@ -116,7 +119,10 @@ __device__ __forceinline__ void qr_update_regs(float4 *y4, const float4 *p4, int
   for (int q = 0; q < NQ; ++q) {
     const int e4 = k4 + glane + QG * q;
     if (q < NQ - 1 || e4 < ap4) {
-      qr_update4(r[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
+      if (q == 0 && edge)
+        qr_update4(r[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, true, s4);
+      else
+        qr_update4(r[q], p4[e4], fct, 4 * e4, k, false, s4);
       y4[e4] = r[q];
     }
   }
