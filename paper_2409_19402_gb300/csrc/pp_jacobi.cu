@@ -798,10 +798,12 @@ cudaError_t launch_shape(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, c
 cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc) {
   const int n4 = a_pad / 4;
   if (GW == 8) {
+    if (n4 <= 32) return query_shape<8, 4>(A, a_pad, C, cc);
     if (n4 <= 40) return query_shape<8, 5>(A, a_pad, C, cc);
     return query_shape<8, 8>(A, a_pad, C, cc);
   }
   if (GW == 16) {
+    if (n4 <= 32) return query_shape<16, 2>(A, a_pad, C, cc);
     if (n4 <= 48) return query_shape<16, 3>(A, a_pad, C, cc);
     if (n4 <= 64) return query_shape<16, 4>(A, a_pad, C, cc);
     return query_shape<16, 8>(A, a_pad, C, cc);
@@ -813,10 +815,12 @@ cudaError_t query(const JacobiArgs &A, int a_pad, int C, int GW, ClusterCfg &cc)
 
 cudaError_t launch(const JacobiArgs &A, int a_pad, const ClusterCfg &cc, cudaStream_t st) {
   if (cc.GW == 8) {
+    if (cc.CW == 4) return launch_shape<8, 4>(A, a_pad, cc, st);
     if (cc.CW == 5) return launch_shape<8, 5>(A, a_pad, cc, st);
     return launch_shape<8, 8>(A, a_pad, cc, st);
   }
   if (cc.GW == 16) {
+    if (cc.CW == 2) return launch_shape<16, 2>(A, a_pad, cc, st);
     if (cc.CW == 3) return launch_shape<16, 3>(A, a_pad, cc, st);
     if (cc.CW == 4) return launch_shape<16, 4>(A, a_pad, cc, st);
     return launch_shape<16, 8>(A, a_pad, cc, st);
