@@ -163,7 +163,7 @@ __global__ void factor_pc_short_kernel(FactorArgs a) {
 
 // ... and the long-side vectors from the slice: long_q(e) = sum_{e2} X(e2, e)
 // u_q(e2) / sigma_q over the short index e2 (X oriented short x long);
-// tile 64 (e) x 32 (q), 256 threads, each 4 x 2 outputs.
+// tile 64 (e) x 32 (q), 256 threads, each 4 x 2 outputs; used for tall slices (l > m).
 __global__ void __launch_bounds__(256) factor_pc_long_kernel(FactorArgs a) {
   const int64_t t = blockIdx.z;
   const Geo g = geo(a, t);
@@ -216,6 +216,65 @@ __global__ void __launch_bounds__(256) factor_pc_long_kernel(FactorArgs a) {
       const float sq = sg[q];
       out[el * g.rank + q] = sq > 0.f ? acc[r][c] / sq : 0.f;
     }
+  }
+}
+
+// The same product when the slice is short x long row-major (l <= m): lanes
+// run over 32 consecutive long indices e (coalesced rows of X), the 8 warps
+// over residues of the short index e2, and the short-side vectors sit in
+// shared memory 8 columns at a time.  Small ragged ranks (the usual output of
+// Alg. 4.2) then cost one pass over the slice per 8 ranks instead of a tile
+// loop over the whole short side per 32.  256 threads; dynamic shared memory
+// holds nshort x 8 vector entries and the 8 x 32 x 8 warp partials.
+constexpr int PCL_QC = 8;
+__global__ void __launch_bounds__(256) factor_pc_long_rows_kernel(FactorArgs a) {
+  const int64_t t = blockIdx.y;
+  const Geo g = geo(a, t);
+  if (g.rank == 0) return;
+  const int64_t nshort = a.l, nlong = a.m;
+  extern __shared__ float4 pcl_smem4[];
+  float4 *Us = pcl_smem4;                                   // nshort x 2 float4
+  float *red = reinterpret_cast<float *>(pcl_smem4 + 2 * nshort);   // [8][32][8]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t e0 = (int64_t)blockIdx.x * 32, e = e0 + lane;
+  const float *Xf = a.X + t * a.l * a.m;
+  const float *sg = a.sig + t * a.b;
+  const float *U = a.Uh + g.uoff;                           // nshort x rank
+  float *out = a.Vh + g.voff;                               // nlong x rank
+  float *Usf = reinterpret_cast<float *>(Us);
+  for (int64_t q0 = 0; q0 < g.rank; q0 += PCL_QC) {
+    for (int64_t idx = tid; idx < nshort * PCL_QC; idx += 256) {
+      const int64_t e2 = idx / PCL_QC, q = q0 + idx % PCL_QC;
+      Usf[idx] = q < g.rank ? U[e2 * g.rank + q] : 0.f;
+    }
+    __syncthreads();
+    float acc[PCL_QC] = {};
+    if (e < nlong) {
+#pragma unroll 4
+      for (int64_t e2 = w; e2 < nshort; e2 += 8) {
+        const float x = Xf[e2 * a.m + e];
+        const float4 u0 = Us[2 * e2], u1 = Us[2 * e2 + 1];
+        acc[0] = fmaf(x, u0.x, acc[0]); acc[1] = fmaf(x, u0.y, acc[1]);
+        acc[2] = fmaf(x, u0.z, acc[2]); acc[3] = fmaf(x, u0.w, acc[3]);
+        acc[4] = fmaf(x, u1.x, acc[4]); acc[5] = fmaf(x, u1.y, acc[5]);
+        acc[6] = fmaf(x, u1.z, acc[6]); acc[7] = fmaf(x, u1.w, acc[7]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < PCL_QC; ++c) red[(w * 32 + lane) * PCL_QC + c] = acc[c];
+    __syncthreads();
+    {
+      const int el = tid / PCL_QC, c = tid % PCL_QC;          // 32 e x 8 q outputs
+      float v = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) v += red[(ww * 32 + el) * PCL_QC + c];
+      const int64_t eo = e0 + el, q = q0 + c;
+      if (eo < nlong && q < g.rank) {
+        const float sq = sg[q];
+        out[eo * g.rank + q] = sq > 0.f ? v / sq : 0.f;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -275,10 +334,17 @@ cudaError_t launch_factors(const FactorArgs &a, cudaStream_t st) {
     factor_pc_short_kernel<<<(unsigned)a.p, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const int64_t nlong = a.l <= a.m ? a.m : a.l;
-    const dim3 g1((unsigned)((R + 31) / 32), (unsigned)((nlong + 63) / 64), (unsigned)a.p);
-    count_launch(1);
-    factor_pc_long_kernel<<<g1, 256, 0, st>>>(a);
+    if (a.l <= a.m) {
+      const size_t smem = sizeof(float) * (size_t)(a.l * PCL_QC + 8 * 32 * PCL_QC);
+      if (smem > 48 * 1024) return cudaErrorInvalidValue;   // qrcp_fits keeps l small
+      count_launch(1);
+      factor_pc_long_rows_kernel<<<dim3((unsigned)((a.m + 31) / 32), (unsigned)a.p), 256, smem,
+                                   st>>>(a);
+    } else {
+      const dim3 g1((unsigned)((R + 31) / 32), (unsigned)((a.l + 63) / 64), (unsigned)a.p);
+      count_launch(1);
+      factor_pc_long_kernel<<<g1, 256, 0, st>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess || !a.Ahk) return e;
     const dim3 g2((unsigned)((a.m + 63) / 64), (unsigned)((a.l + 63) / 64), (unsigned)a.p);
