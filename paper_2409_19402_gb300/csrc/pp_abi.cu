@@ -262,8 +262,15 @@ float default_tol(int64_t l, int64_t m) {
 }
 
 // Steps shared by Alg. 4.1 and Alg. 4.2 up to the facewise SVD.
+// Partial-sum counts of the energies |A|^2, |A-hat|^2 and |A - A_k|^2 when
+// their final sums are left to the report kernel (one launch instead of three).
+struct EnergyParts {
+  int np_a = 0, np_h = 0, np_e = 0;
+};
+
 pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
-                          int64_t p, const Opts &o, const DecompWs &w, cudaStream_t st) {
+                          int64_t p, const Opts &o, const DecompWs &w, cudaStream_t st,
+                          EnergyParts *defer = nullptr) {
   PP_TRY(cudaMemsetAsync(w.status, 0, sizeof(int32_t), st));
   if (o.check_q) PP_TRY(pp::launch_check_q(Q, n, p, o.q_tol, w.status, st));
   if (o.check_finite) PP_TRY(pp::launch_check_finite(A, n * l * m, w.status, st));
@@ -272,8 +279,13 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   int np_h = 0, np_a = 0;
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_h, w.part_a,
                              &np_a, w.part_h, w.status, st));
-  PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
-  PP_TRY(pp::launch_sum_partials(w.part_h, np_h, w.scal + 1, st));
+  if (defer) {
+    defer->np_a = np_a;
+    defer->np_h = np_h;
+  } else {
+    PP_TRY(pp::launch_sum_partials(w.part_a, np_a, w.scal + 0, st));
+    PP_TRY(pp::launch_sum_partials(w.part_h, np_h, w.scal + 1, st));
+  }
   stage(1, st);
   // step 3: facewise SVD -- one-sided Jacobi, on the rows of R from a QR with
   // column pivoting of each slice where the slice fits that kernel
@@ -308,13 +320,29 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
 
 // Back-projection A_k = A-hat_k x_3 Q with the fused error |A - A_k|^2.
 pp_status backproject(const float *A, const float *Q, int64_t l, int64_t m, int64_t n,
-                      int64_t p, float *Ak, const DecompWs &w, cudaStream_t st) {
+                      int64_t p, float *Ak, const DecompWs &w, cudaStream_t st,
+                      EnergyParts *defer = nullptr) {
   int np = 0;
   // M(r, c) = Q(r, c) = Q[r*p + c]
   PP_TRY(pp::launch_mode3_tc(Q, p, 1, w.Ahk, Ak, n, p, l * m, A, w.part_e, &np, nullptr, nullptr,
                              nullptr, w.status, st));
-  PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 2, st));
+  if (defer)
+    defer->np_e = np;
+  else
+    PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 2, st));
   return PP_OK;
+}
+
+// The report's energies from the deferred partial sums (written to scal[0..2]
+// as well), or nothing to do when no report is wanted.
+void report_energies(pp::ReportArgs &ra, const DecompWs &w, const EnergyParts &ep) {
+  ra.parts[0] = w.part_a;
+  ra.parts[1] = w.part_h;
+  ra.parts[2] = w.part_e;
+  ra.nparts[0] = ep.np_a;
+  ra.nparts[1] = ep.np_h;
+  ra.nparts[2] = ep.np_e;
+  ra.sums = w.scal;
 }
 
 // ---- complex Q (pp_complex.cu)
@@ -623,8 +651,9 @@ pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m, int6
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
   const DecompWs w = carve_decomp(c, l, m, n, p, false, o.precond >= 0);
+  EnergyParts ep;
   stage(0, st);
-  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st, rep ? &ep : nullptr)) return e;
   stage(3, st);
   pp::FactorArgs fa = decomp_factor_args(w, l, m, p);
   fa.kfix = k;
@@ -638,7 +667,7 @@ pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m, int6
   fa.disc_partial = w.disc_p;
   PP_TRY(pp::launch_factors(fa, st));
   stage(4, st);
-  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st)) return e;
+  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st, rep ? &ep : nullptr)) return e;
   if (rep) {
     pp::ReportArgs ra;
     ra.rep = rep;
@@ -654,6 +683,7 @@ pp_status tsvdq_trunc(const float *A, const float *Q, int64_t l, int64_t m, int6
     ra.K = nullptr;
     ra.kappa_fixed = k * p;
     ra.offs = nullptr;
+    report_energies(ra, w, ep);
     PP_TRY(pp::launch_report(ra, st));
   }
   stage(5, st);
@@ -676,8 +706,9 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
   const DecompWs w = carve_decomp(c, l, m, n, p, true, o.precond >= 0);
+  EnergyParts ep;
   stage(0, st);
-  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st)) return e;
+  if (pp_status e = project_and_svd(A, Q, l, m, n, p, o, w, st, rep ? &ep : nullptr)) return e;
   // Alg. 4.2 steps 4-7
   pp::SelectArgs sa;
   sa.sig = w.sig;
@@ -705,7 +736,7 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
   fa.disc_partial = nullptr;
   PP_TRY(pp::launch_factors(fa, st));
   stage(4, st);
-  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st)) return e;
+  if (pp_status e = backproject(A, Q, l, m, n, p, Ak, w, st, rep ? &ep : nullptr)) return e;
   if (rep) {
     pp::ReportArgs ra;
     ra.rep = rep;
@@ -721,6 +752,7 @@ pp_status tsvdqII(const float *A, const float *Q, int64_t l, int64_t m, int64_t 
     ra.K = w.K;
     ra.kappa_fixed = -1;
     ra.offs = offs;
+    report_energies(ra, w, ep);
     PP_TRY(pp::launch_report(ra, st));
   }
   stage(5, st);

@@ -220,6 +220,12 @@ struct ReportArgs {
   const int64_t *K;
   int64_t kappa_fixed;                        // k*p for trunc, -1 for ragged (from offs)
   const int64_t *offs;
+  // energies still as partial sums: when parts[i] is set the report kernel sums
+  // them (the same fixed order as launch_sum_partials), uses the sum in place of
+  // normA2 / normAh2 / err2 (i = 0, 1, 2) and stores it to sums[i]
+  const double *parts[3] = {nullptr, nullptr, nullptr};
+  int nparts[3] = {0, 0, 0};
+  double *sums = nullptr;
 };
 cudaError_t launch_report(const ReportArgs &a, cudaStream_t st);
 

@@ -20,7 +20,9 @@
 // threads then apply the reflector to the unpivoted vectors, 4 lanes per
 // vector, recompute their trailing norms from the updated entries (no norm
 // downdating, hence no cancellation safeguard) and leave the next candidates.
-// One barrier per step; R is written at the end.
+// The unpivoted vectors stay packed in the lowest 4-lane groups (the group
+// that held the pivot takes over the last group's vector), so the warps past
+// them have nothing to issue.  One barrier per step; R is written at the end.
 #include "pp_internal.h"
 
 namespace pp {
@@ -36,7 +38,7 @@ constexpr int QR_SMEM_BUDGET = 200 * 1024;
 __host__ __device__ inline int64_t qr_ap(int64_t a) { return (a + 31) / 32 * 32 + 16; }
 
 __host__ __device__ inline int64_t qr_smem_floats(int64_t b, int64_t a) {
-  return b * qr_ap(a) + 3 * b;               // vectors, diagonal, used flags, order
+  return b * qr_ap(a) + 4 * b;               // vectors, diagonal, order, 2 group maps
 }
 
 constexpr int QR_NREG = 11;                  // float4 per lane held in registers in the update
@@ -139,8 +141,8 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
   const int ap = (int)qr_ap(a), ap4 = ap / 4;
   float *Y = qs;                             // vector j (original index) at Y + j * ap
   float *diag = Y + (size_t)b * ap;          // R(k, k)
-  int *used = reinterpret_cast<int *>(diag + b);   // vector j already pivoted
-  int *order = used + b;                     // pivoted position -> vector
+  int *order = reinterpret_cast<int *>(diag + b);  // pivoted position -> vector
+  int *gmap = order + b;                     // [2][b]: group -> vector, by step parity
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int glane = tid % QG, grp = tid / QG, ngrp = QR_THREADS / QG;
   const unsigned gmask = ((1u << QG) - 1u) << (lane & ~(QG - 1));
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
     for (int idx = tid; idx < b * (ap - a); idx += QR_THREADS)
       Y[(size_t)(idx / (ap - a)) * ap + a + idx % (ap - a)] = 0.f;
   }
-  for (int j = tid; j < b; j += QR_THREADS) used[j] = 0;
+  for (int j = tid; j < b; j += QR_THREADS) gmap[j] = j;
   __syncthreads();
   {
     float bestv = 0.f;
@@ -208,15 +210,21 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
     const float beta = vtv > 0.f ? __fdividef(2.f, vtv) : 0.f;
     if (tid == 0) {
       diag[k] = alpha;
-      used[sp] = 1;
       order[k] = sp;
     }
     const bool in_regs = ap4 - k4 <= QG * QR_NREG;
     const int nq = (ap4 - k4 + QG - 1) / QG;
     float bestv = 0.f;
     unsigned bestj = QR_NONE;
-    for (int j = grp; j < b; j += ngrp) {
-      if (j == sp || used[j]) continue;
+    // b - k vectors were live at this step, the pivot among them; its group
+    // takes the last group's vector and the remaining b - k - 1 stay packed
+    const int nlive = b - k - 1;
+    const int *gcur = gmap + par * b;
+    int *gnext = gmap + (par ^ 1) * b;
+    for (int g = grp; g < nlive; g += ngrp) {
+      int j = gcur[g];
+      if (j == sp) j = gcur[nlive];
+      if (glane == 0) gnext[g] = j;
       float4 *y4 = reinterpret_cast<float4 *>(Y + (size_t)j * ap);
       float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f), s4 = c4;
       if (in_regs) {                           // one read and one write of the vector
@@ -251,7 +259,10 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
       float s = (s4.x + s4.y) + (s4.z + s4.w);
 #pragma unroll
       for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
-      if (bestj == QR_NONE || s > bestv) { bestv = s; bestj = (unsigned)j; }
+      if (bestj == QR_NONE || s > bestv || (s == bestv && (unsigned)j < bestj)) {
+        bestv = s;
+        bestj = (unsigned)j;
+      }
     }
     warp_pivot(bestv, bestj, bv, bj);
     if (lane == 0) { cand_v[par ^ 1][warp] = bv; cand_j[par ^ 1][warp] = bj; }

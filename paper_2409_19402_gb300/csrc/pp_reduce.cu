@@ -69,16 +69,30 @@ __global__ void check_finite_kernel(const float *__restrict__ x, int64_t n, int3
   if (__syncthreads_or(bad) && threadIdx.x == 0) set_status(status, PP_ENONFINITE);
 }
 
-__global__ void report_kernel(ReportArgs a) {
+// the sum of n partials in the order of sum_partials_kernel (blockDim 1024)
+__device__ __forceinline__ double sum_partials_block(const double *partials, int n) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  return block_sum(acc);
+}
+
+__global__ void __launch_bounds__(1024) report_kernel(ReportArgs a) {
+  double e[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (a.parts[i]) e[i] = sum_partials_block(a.parts[i], a.nparts[i]);
   if (threadIdx.x != 0) return;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    if (a.parts[i]) a.sums[i] = e[i];
   pp_report r;
   r.status = *a.status;
   int32_t sw = 0;
   for (int64_t t = 0; t < a.p; ++t) sw = max(sw, a.sweeps[t]);
   r.sweeps = sw;
-  r.normA2 = *a.normA2;
-  r.normAh2 = *a.normAh2;
-  r.err2 = a.err2 ? *a.err2 : -1.0;
+  r.normA2 = a.parts[0] ? e[0] : *a.normA2;
+  r.normAh2 = a.parts[1] ? e[1] : *a.normAh2;
+  r.err2 = a.parts[2] ? e[2] : (a.err2 ? *a.err2 : -1.0);
   if (a.sel_scal) {
     r.K = *a.K;
     r.kappa = a.offs[a.p];
@@ -154,7 +168,7 @@ cudaError_t launch_check_finite(const float *x, int64_t n, int32_t *status, cuda
 
 cudaError_t launch_report(const ReportArgs &a, cudaStream_t st) {
   count_launch(1);
-  report_kernel<<<1, 32, 0, st>>>(a);
+  report_kernel<<<1, 1024, 0, st>>>(a);
   return cudaGetLastError();
 }
 

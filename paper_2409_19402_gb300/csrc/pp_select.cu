@@ -15,8 +15,10 @@
 // in FP64 from the FP32 sigma (exact: a 24-bit significand squared fits).
 //
 // The cumulative sums run in FP64 in one CTA: 1024 contiguous chunks summed
-// sequentially, a fixed-order scan of the chunk sums, then a second pass over
-// each chunk to find the first crossing.  The result is deterministic.
+// sequentially, a fixed-order scan of the chunk sums (warp shuffles, then the
+// warp totals), then a second pass over each chunk to find the first crossing.
+// rho_t is read off where the slice's ranks cross K (ranks increase along a
+// slice), one writer per slice.  The result is deterministic.
 #include "pp_internal.h"
 
 namespace pp {
@@ -72,26 +74,65 @@ __global__ void select_rank_kernel(const float *__restrict__ sig, int64_t p, int
   }
 }
 
-// Inclusive scan of v over the CTA in a fixed order (Hillis-Steele in shared memory).
-__device__ double block_inclusive_scan(double v, double *buf) {
-  const int tid = threadIdx.x;
-  buf[tid] = v;
-  __syncthreads();
-  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-    const double add = tid >= off ? buf[tid - off] : 0.0;
-    __syncthreads();
-    buf[tid] += add;
-    __syncthreads();
+// Inclusive scan of v over the CTA in a fixed order: a shuffle scan inside each
+// warp, the warp totals scanned by warp 0, their prefix added back.
+__device__ double block_inclusive_scan(double v, double *wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += u;
   }
-  const double r = buf[tid];
+  if (lane == 31) wsum[warp] = v;
   __syncthreads();
-  return r;
+  if (warp == 0) {
+    double w = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const double u = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += u;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) v += wsum[warp - 1];
+  __syncthreads();                            // wsum is reused by the next scan
+  return v;
+}
+
+// The same scan for integers (exact in any order).
+__device__ int64_t block_inclusive_scan_i64(int64_t v, int64_t *wsum) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int64_t u = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += u;
+  }
+  if (lane == 31) wsum[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    int64_t w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int64_t u = __shfl_up_sync(0xffffffffu, w, off);
+      if (lane >= off) w += u;
+    }
+    wsum[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) v += wsum[warp - 1];
+  __syncthreads();
+  return v;
 }
 
 __global__ void __launch_bounds__(SEL_THREADS) select_finish_kernel(
     const double *__restrict__ keys_sorted, const int32_t *__restrict__ rank, int64_t p, int b,
     double gamma, int32_t *__restrict__ rho, int64_t *__restrict__ offs, double *__restrict__ scal,
     int64_t *__restrict__ Kout) {
+  __shared__ double wsum[32];
+  __shared__ int64_t isum[32];
   __shared__ double buf[SEL_THREADS];
   __shared__ unsigned long long Ksh;
   __shared__ double keptsh;
@@ -101,22 +142,29 @@ __global__ void __launch_bounds__(SEL_THREADS) select_finish_kernel(
   const int64_t lo = tid * chunk, hi = min(N, lo + chunk);
   double s = 0.0;
   for (int64_t q = lo; q < hi; ++q) s += keys_sorted[q];
-  const double incl = block_inclusive_scan(s, buf);
-  // the exclusive prefix of a chunk is the previous thread's inclusive value
-  buf[tid] = incl;
+  // the exclusive prefix of a chunk is the previous thread's inclusive value,
+  // so that the running sums below continue exactly where the scan left them
+  buf[tid] = block_inclusive_scan(s, wsum);
   if (tid == 0) { Ksh = 0xffffffffffffffffull; keptsh = 0.0; }
   __syncthreads();
   const double total = buf[SEL_THREADS - 1];
   const double before = tid == 0 ? 0.0 : buf[tid - 1];
-  __syncthreads();
-  if (total > 0.0) {
+  if (total > 0.0 && lo < hi) {
+    // running sums c_q = before + k_lo + ... + k_q in this order; a chunk whose
+    // prefix already reaches the threshold crosses at its first key (keys are
+    // >= 0), so only the chunks before the crossing walk their keys (FP64 is
+    // a narrow pipe on this part)
     const double thresh = gamma * total;
-    double c = before;
-    for (int64_t q = lo; q < hi; ++q) {
-      c += keys_sorted[q];
-      if (c >= thresh) {
-        atomicMin(&Ksh, (unsigned long long)(q + 1));
-        break;
+    if (before >= thresh) {
+      atomicMin(&Ksh, (unsigned long long)(lo + 1));
+    } else {
+      double c = before;
+      for (int64_t q = lo; q < hi; ++q) {
+        c += keys_sorted[q];
+        if (c >= thresh) {
+          atomicMin(&Ksh, (unsigned long long)(q + 1));
+          break;
+        }
       }
     }
   }
@@ -129,15 +177,15 @@ __global__ void __launch_bounds__(SEL_THREADS) select_finish_kernel(
     for (int64_t q = lo; q < K; ++q) c += keys_sorted[q];
     keptsh = c;
   }
-  __syncthreads();
-  // per-slice ranks: rank[t*b + j] increases with j, count entries with rank < K
-  for (int64_t t = tid; t < p; t += SEL_THREADS) {
-    int lo2 = 0, hi2 = b;
-    while (lo2 < hi2) {
-      const int mid = (lo2 + hi2) >> 1;
-      if (rank[t * b + mid] < K) lo2 = mid + 1; else hi2 = mid;
-    }
-    rho[t] = lo2;
+  // per-slice ranks: rank[t*b + j] increases with j, so rho_t is the j where
+  // the slice's ranks cross K; exactly one entry of each slice writes it
+  for (int64_t e = tid; e < N; e += SEL_THREADS) {
+    const int64_t t = e / b;
+    const int j = (int)(e % b);
+    const bool in = rank[e] < K;
+    const bool next_in = j + 1 < b && rank[e + 1] < K;
+    if (in && !next_in) rho[t] = j + 1;
+    if (j == 0 && !in) rho[t] = 0;
   }
   __syncthreads();
   // offsets: exclusive scan of rho over p slices (chunked like the energies)
@@ -145,13 +193,13 @@ __global__ void __launch_bounds__(SEL_THREADS) select_finish_kernel(
   const int64_t plo = tid * pchunk, phi = min(p, plo + pchunk);
   int64_t cnt = 0;
   for (int64_t t = plo; t < phi; ++t) cnt += rho[t];
-  const double inc2 = block_inclusive_scan((double)cnt, buf);   // exact: integers < 2^53
-  int64_t run = (int64_t)inc2 - cnt;
+  const int64_t inc2 = block_inclusive_scan_i64(cnt, isum);
+  int64_t run = inc2 - cnt;
   for (int64_t t = plo; t < phi; ++t) {
     offs[t] = run;
     run += rho[t];
   }
-  if (tid == SEL_THREADS - 1) offs[p] = (int64_t)inc2;
+  if (tid == SEL_THREADS - 1) offs[p] = inc2;
   if (tid == 0) {
     scal[0] = keptsh;
     scal[1] = total;
@@ -165,8 +213,10 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t st) {
   const int64_t N = a.p * a.b;
   const size_t smem_need = (size_t)N * sizeof(float);
   const int use_smem = smem_need <= 160 * 1024;
-  int blocks = (int)((N + 7) / 8);          // 8 warps (entries) per 256-thread block
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  // at most one CTA per SM: each CTA stages all of sigma once, its 32 warps
+  // then take entries in turn
+  int blocks = (int)((N + 31) / 32);
+  if (blocks > 152) blocks = 152;
   cudaError_t e;
   if (use_smem) {
     e = cudaFuncSetAttribute(select_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -174,7 +224,7 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
   }
   count_launch(1);
-  select_rank_kernel<<<blocks, 256, use_smem ? smem_need : 0, st>>>(
+  select_rank_kernel<<<blocks, 1024, use_smem ? smem_need : 0, st>>>(
       a.sig, a.p, (int)a.b, a.keys_sorted, a.rank, use_smem);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
