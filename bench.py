@@ -339,7 +339,10 @@ def run_ours(args):
     jac_ms = stage_mean[1]
     flops = nominal_svd_flops(L, M, P)
     achieved = flops / (jac_ms / 1e3) / 1e12
-    stage_kernels = (["qrcp_kernel"] if tuned[3] else []) + ["jacobi_cluster_kernel"]
+    # the QR kernel that runs for this slice shape: register-resident up to 128
+    # vectors of up to 176 entries, else the shared-memory one
+    qr_kernel = "qrcp_reg_kernel" if min(L, M) <= 128 and max(L, M) <= 176 else "qrcp_kernel"
+    stage_kernels = ([qr_kernel] if tuned[3] else []) + ["jacobi_cluster_kernel"]
     roofline = {"kernel": " + ".join(stage_kernels) + " (facewise SVD stage)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": stage_traffic(stage_kernels),

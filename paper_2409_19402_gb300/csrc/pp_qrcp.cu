@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
   const int l = (int)A.l, m = (int)A.m;
   const bool rows = l <= m;
   const int b = rows ? l : m, a = rows ? m : l;
-  const int ap = (int)qr_ap(a), ap4 = ap / 4;
+  const int ap = (int)qr_ap(a);
+  const int ap4 = (a + 3) / 4;   // float4 holding entries (the zero padding past them is skipped)
   float *Y = qs;                             // vector j (original index) at Y + j * ap
   float *diag = Y + (size_t)b * ap;          // R(k, k)
   int *order = reinterpret_cast<int *>(diag + b);  // pivoted position -> vector
@@ -278,6 +279,226 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_kernel(QrArgs A) {
   for (int j = tid; j < b; j += QR_THREADS) A.qperm[f * b + j] = order[j];
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for slices of at most QR_REG_MAXB vectors of at
+// most 4 * 4 * QR_REG_NCH entries (the video-shaped 120 x 160 slices): a 4-lane
+// group keeps one vector in registers, lane glane holding float4 chunks
+// glane, glane + 4, ... of it, so the rank-1 updates touch no shared memory.
+// After each step every warp publishes only its pivot candidate (the vector,
+// its trailing norm, its index and its group) in a parity-buffered slot; the
+// next step reads the reflector from the winning slot and writes R's column k
+// from it.  The unpivoted vectors stay packed in the lowest groups: when the
+// pivot's group is not the last live one, the last live group hands its
+// updated vector to the pivot's group through a parity-buffered slot, taken up
+// at the next step.  Same pivot rule, reflector and norms as qrcp_kernel (the
+// chunks are split over the lanes differently, so sums round in another order).
+constexpr int QR_REG_MAXB = QR_THREADS / QG;    // one vector per group
+constexpr int QR_REG_NCH = 11;                  // float4 chunks per lane, at most
+constexpr int QR_REG_A4 = QG * QR_REG_NCH;      // float4 per vector (<= 176 entries)
+
+__host__ __device__ inline int64_t qr_reg_smem_bytes(int64_t b, int64_t a) {
+  // candidate slots [2][NW] and hand-over slots [2], then staging / R, diag, order
+  return (int64_t)sizeof(float4) * (2 * (QR_THREADS / 32) + 2) * QR_REG_A4 +
+         (int64_t)sizeof(float) * (b * qr_ap(a) + 2 * b);
+}
+
+// one Householder update of the register-resident vector v (NCH chunks per
+// lane) from the chunk that holds entry k on (Q0 = k4 / 4)
+template <int NCH, int Q0>
+__device__ __forceinline__ void qr_reg_update(float4 (&v)[NCH], const float4 *p4, int k4, int k,
+                                              float vk, float beta, int glane, unsigned gmask,
+                                              int a4, float4 &s4) {
+  float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int q = Q0; q < NCH; ++q) {
+    const int e4 = glane + QG * q;
+    if ((q > Q0 || e4 >= k4) && (q < NCH - 1 || e4 < a4)) {
+      const float4 h = q == Q0 ? qr_h4(p4, e4, k4, k, vk) : p4[e4];
+      c4.x = fmaf(h.x, v[q].x, c4.x);
+      c4.y = fmaf(h.y, v[q].y, c4.y);
+      c4.z = fmaf(h.z, v[q].z, c4.z);
+      c4.w = fmaf(h.w, v[q].w, c4.w);
+    }
+  }
+  float c = (c4.x + c4.y) + (c4.z + c4.w);
+#pragma unroll
+  for (int o = QG / 2; o > 0; o >>= 1) c += __shfl_xor_sync(gmask, c, o, QG);
+  const float fct = beta * c;
+#pragma unroll
+  for (int q = Q0; q < NCH; ++q) {
+    const int e4 = glane + QG * q;
+    if ((q > Q0 || e4 >= k4) && (q < NCH - 1 || e4 < a4)) {
+      if (q == Q0)
+        qr_update4(v[q], qr_h4(p4, e4, k4, k, vk), fct, 4 * e4, k, e4 == k4, s4);
+      else
+        qr_update4(v[q], p4[e4], fct, 4 * e4, k, false, s4);
+    }
+  }
+}
+
+template <int NCH>
+__device__ __forceinline__ void qr_reg_store(float4 *dst, const float4 (&v)[NCH], int glane,
+                                             int a4) {
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int e4 = glane + QG * q;
+    if (q < NCH - 1 || e4 < a4) dst[e4] = v[q];
+  }
+}
+
+template <int NCH>
+__device__ __forceinline__ void qr_reg_load(float4 (&v)[NCH], const float4 *src, int glane,
+                                            int a4) {
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int e4 = glane + QG * q;
+    v[q] = (q < NCH - 1 || e4 < a4) ? src[e4] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// NCH = float4 chunks per lane: a4 = ceil(a / 4) <= 4 * NCH
+template <int NCH>
+__global__ void __launch_bounds__(QR_THREADS) qrcp_reg_kernel(QrArgs A) {
+  extern __shared__ __align__(16) float qs[];
+  constexpr int NW = QR_THREADS / 32;
+  __shared__ unsigned cand_v[2][NW], cand_j[2][NW], cand_g[2][NW];
+  __shared__ int move_j[2];
+  const int64_t f = blockIdx.x;
+  const int l = (int)A.l, m = (int)A.m;
+  const bool rows = l <= m;
+  const int b = rows ? l : m, a = rows ? m : l;
+  const int ap = (int)qr_ap(a);
+  const int a4 = (a + 3) / 4;
+  float4 *cvec = reinterpret_cast<float4 *>(qs);        // [2][NW][QR_REG_A4] candidates
+  float4 *mvec = cvec + 2 * NW * QR_REG_A4;             // [2][QR_REG_A4] hand-over
+  float *Y = reinterpret_cast<float *>(mvec + 2 * QR_REG_A4);   // staging b x ap, then R b x b
+  float *diag = Y + (size_t)b * ap;
+  int *order = reinterpret_cast<int *>(diag + b);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int glane = tid % QG, g = tid / QG;
+  const unsigned gmask = ((1u << QG) - 1u) << (lane & ~(QG - 1));
+  const float *Xf = A.X + f * (int64_t)l * m;
+
+  if (rows) {
+    for (int idx = tid; idx < b * ap; idx += QR_THREADS) {
+      const int j = idx / ap, e = idx % ap;
+      Y[idx] = e < a ? Xf[(int64_t)j * m + e] : 0.f;
+    }
+  } else {
+    for (int idx = tid; idx < b * a; idx += QR_THREADS) {
+      const int e = idx / b, j = idx % b;
+      Y[(size_t)j * ap + e] = Xf[(int64_t)e * m + j];
+    }
+    for (int idx = tid; idx < b * (ap - a); idx += QR_THREADS)
+      Y[(size_t)(idx / (ap - a)) * ap + a + idx % (ap - a)] = 0.f;
+  }
+  __syncthreads();
+  int myj = g;                        // vector held by this group
+  float4 v[NCH];
+  {
+    const bool live = g < b;
+    qr_reg_load<NCH>(v, reinterpret_cast<const float4 *>(Y + (size_t)(live ? g : 0) * ap), glane,
+                     a4);
+    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      s4.x = fmaf(v[q].x, v[q].x, s4.x);
+      s4.y = fmaf(v[q].y, v[q].y, s4.y);
+      s4.z = fmaf(v[q].z, v[q].z, s4.z);
+      s4.w = fmaf(v[q].w, v[q].w, s4.w);
+    }
+    float s = (s4.x + s4.y) + (s4.z + s4.w);
+#pragma unroll
+    for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
+    unsigned bv, bj;
+    warp_pivot(s, live ? (unsigned)g : QR_NONE, bv, bj);
+    if (live && (unsigned)g == bj) qr_reg_store<NCH>(cvec + (size_t)warp * QR_REG_A4, v, glane, a4);
+    if (lane == 0) {
+      cand_v[0][warp] = bv;
+      cand_j[0][warp] = bj;
+      cand_g[0][warp] = bj;           // group == vector before any hand-over
+    }
+  }
+  __syncthreads();
+
+  int gs_prev = -1, gl_prev = -1;     // last step's pivot group and hand-over source
+  for (int k = 0; k < b; ++k) {
+    const int k4 = k / 4;
+    const int par = k & 1;
+    // take up the vector handed over at the previous step
+    if (gs_prev >= 0 && g == gs_prev) {
+      qr_reg_load<NCH>(v, mvec + (size_t)par * QR_REG_A4, glane, a4);
+      myj = move_j[par];
+    }
+    const bool has = lane < NW;
+    const unsigned cj = has ? cand_j[par][lane] : QR_NONE;
+    unsigned bv, bj;
+    warp_pivot(has ? __uint_as_float(cand_v[par][lane]) : 0.f, cj, bv, bj);
+    const unsigned hit = __ballot_sync(0xffffffffu, has && cj == bj && bj != QR_NONE);
+    const int wi = hit ? __ffs(hit) - 1 : 0;
+    const int sp = bj < (unsigned)b ? (int)bj : 0;
+    int gs = (int)cand_g[par][wi];    // group that published the pivot ...
+    if (gs == gl_prev) gs = gs_prev;  // ... unless it has handed it over since
+    const float4 *p4 = cvec + ((size_t)par * NW + wi) * QR_REG_A4;
+    const float *pf = reinterpret_cast<const float *>(p4);
+    const float x0 = pf[k];
+    const float nx = sqrtf(__uint_as_float(bv));
+    const float alpha = x0 >= 0.f ? -nx : nx;
+    const float vk = x0 - alpha;
+    const float vtv = 2.f * nx * (nx + fabsf(x0));
+    const float beta = vtv > 0.f ? __fdividef(2.f, vtv) : 0.f;
+    if (tid == 0) {
+      diag[k] = alpha;
+      order[k] = sp;
+    }
+    for (int e = tid; e < k; e += QR_THREADS) Y[(size_t)e * b + k] = pf[e];   // R(e, k)
+    // groups 0 .. b-k-1 hold the b-k unpivoted vectors; the pivot's is done
+    const bool live = g < b - k && g != gs;
+    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+      switch (k4 / QG) {                      // uniform in the CTA
+#define QR_RCASE(Q0)                                                              \
+  case Q0:                                                                        \
+    if (Q0 < NCH) qr_reg_update<NCH, (Q0 < NCH ? Q0 : 0)>(v, p4, k4, k, vk, beta, \
+                                                          glane, gmask, a4, s4);  \
+    break;
+        QR_RCASE(0) QR_RCASE(1) QR_RCASE(2) QR_RCASE(3) QR_RCASE(4) QR_RCASE(5)
+        QR_RCASE(6) QR_RCASE(7)
+#undef QR_RCASE
+        default: break;
+      }
+    }
+    float s = (s4.x + s4.y) + (s4.z + s4.w);
+#pragma unroll
+    for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
+    warp_pivot(s, live ? (unsigned)myj : QR_NONE, bv, bj);
+    if (live && (unsigned)myj == bj)
+      qr_reg_store<NCH>(cvec + ((size_t)(par ^ 1) * NW + warp) * QR_REG_A4, v, glane, a4);
+    if (lane == 0) {
+      cand_v[par ^ 1][warp] = bv;
+      cand_j[par ^ 1][warp] = bj;
+    }
+    // the warp's candidate group (the one whose vector won the warp)
+    const unsigned won = __ballot_sync(0xffffffffu, live && (unsigned)myj == bj);
+    if (lane == 0 && won) cand_g[par ^ 1][warp] = (unsigned)(warp * (32 / QG) + (__ffs(won) - 1) / QG);
+    // hand the last live group's vector to the pivot's group
+    const int gl = b - k - 1;
+    if (gl != gs && g == gl) {
+      qr_reg_store<NCH>(mvec + (size_t)(par ^ 1) * QR_REG_A4, v, glane, a4);
+      if (glane == 0) move_j[par ^ 1] = myj;
+    }
+    gs_prev = gl != gs ? gs : -1;
+    gl_prev = gl != gs ? gl : -1;
+    __syncthreads();
+  }
+  float *Rf = A.R + f * (int64_t)b * b;
+  for (int idx = tid; idx < b * b; idx += QR_THREADS) {
+    const int i = idx / b, j = idx % b;
+    Rf[idx] = j < i ? 0.f : (j == i ? diag[j] : Y[idx]);
+  }
+  for (int j = tid; j < b; j += QR_THREADS) A.qperm[f * b + j] = order[j];
+}
+
 }  // namespace
 
 bool qrcp_fits(int64_t l, int64_t m) {
@@ -287,6 +508,20 @@ bool qrcp_fits(int64_t l, int64_t m) {
 
 cudaError_t launch_qrcp(const QrArgs &A, cudaStream_t st) {
   const int64_t b = A.l < A.m ? A.l : A.m, a = A.l < A.m ? A.m : A.l;
+  const int64_t nch = ((a + 3) / 4 + QG - 1) / QG;   // float4 chunks per lane
+  if (b <= QR_REG_MAXB && nch <= QR_REG_NCH) {
+    const size_t rsmem = (size_t)qr_reg_smem_bytes(b, a);
+    auto kern = nch <= 4 ? qrcp_reg_kernel<4>
+              : nch <= 6 ? qrcp_reg_kernel<6>
+              : nch <= 8 ? qrcp_reg_kernel<8>
+              : nch <= 10 ? qrcp_reg_kernel<10> : qrcp_reg_kernel<11>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)rsmem);
+    if (e != cudaSuccess) return e;
+    count_launch(1);
+    kern<<<(unsigned)A.p, QR_THREADS, rsmem, st>>>(A);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(float) * (size_t)qr_smem_floats(b, a);
   cudaError_t e = cudaFuncSetAttribute(qrcp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
