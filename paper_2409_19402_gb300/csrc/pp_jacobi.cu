@@ -440,6 +440,49 @@ __device__ __forceinline__ bool jacobi_pair_reg(float4 (&xv)[CW], float &al,
   return true;
 }
 
+// The last round of a cross pass with the blocks' next seats known: the same
+// rotation (or none) as jacobi_pair_reg, after which the bottom vector and its
+// tracked norm are always stored to (yo, nbo), its seat for the next block
+// round in this CTA or another CTA of the cluster.
+template <int GW, int CW>
+__device__ __forceinline__ bool jacobi_pair_reg_out(float4 (&xv)[CW], float &al,
+                                                    const float *__restrict__ y, const float *nb,
+                                                    float *yo, float *nbo, int n4, float tol2,
+                                                    int lane, unsigned mask, float *wred) {
+  float4 yv[CW];
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) {
+      yv[q] = reinterpret_cast<const float4 *>(y)[e4];
+      g0 = fmaf(xv[q].x, yv[q].x, g0);
+      g1 = fmaf(xv[q].y, yv[q].y, g1);
+      g2 = fmaf(xv[q].z, yv[q].z, g2);
+      g3 = fmaf(xv[q].w, yv[q].w, g3);
+    }
+  }
+  const float g = group_sum_smem<GW>((g0 + g1) + (g2 + g3), wred, mask);
+  float be = *nb;
+  const bool rot = !(g == 0.f || g * g <= tol2 * al * be);
+  if (rot) {
+    float t, s, tau;
+    pair_angle(g, al, be, t, s, tau);
+#pragma unroll
+    for (int q = 0; q < CW; ++q)
+      if (lane + GW * q < n4) rotate4(xv[q], yv[q], s, tau);
+    al = fmaxf(fmaf(-t, g, al), 0.f);
+    be = fmaf(t, g, be);
+  }
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    const int e4 = lane + GW * q;
+    if (e4 < n4) reinterpret_cast<float4 *>(yo)[e4] = yv[q];
+  }
+  if (lane == 0) *nbo = be;
+  return rot;
+}
+
 // squared norms of `count` vectors (rows of a_pad floats), one warp per vector
 __device__ void block_norms(const float *v, float *nrm, int count, int n4) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -486,9 +529,17 @@ __device__ int cross_pass_warp(float *top, float *bot, float *ntop, float *nbot,
 // the bottom vectors travel through shared memory; the top vectors and their
 // norms are written back once at the end.  Needs blockDim.x / GW >= bs.  The
 // arithmetic is that of cross_pass_warp, so the results are identical.
-template <int GW, int CW>
+//
+// SEATS: the blocks' seats for the next block round (rtop, rntop, rbot, rnbot,
+// possibly in other CTAs of the cluster) are known, and the last round stores
+// each bottom vector there and the top vectors go there from the registers,
+// in place of the local write-back and a separate block copy; the caller's
+// cluster barrier then orders those stores.
+template <int GW, int CW, bool SEATS = false>
 __device__ int cross_pass_reg(float *top, float *bot, float *ntop, float *nbot, int bs,
-                              int a_pad, float tol2, float *wred) {
+                              int a_pad, float tol2, float *wred, float *rtop = nullptr,
+                              float *rntop = nullptr, float *rbot = nullptr,
+                              float *rnbot = nullptr) {
   const int lane = threadIdx.x % GW, i = threadIdx.x / GW;
   const unsigned mask = group_mask<GW>();
   const int n4 = a_pad / 4;
@@ -505,7 +556,7 @@ __device__ int cross_pass_reg(float *top, float *bot, float *ntop, float *nbot, 
     al = ntop[i];
   }
   int rot = 0;
-  for (int r = 0; r < bs; ++r) {
+  for (int r = 0; r < (SEATS ? bs - 1 : bs); ++r) {
     if (act) {
       int j = i + r;
       if (j >= bs) j -= bs;
@@ -515,6 +566,25 @@ __device__ int cross_pass_reg(float *top, float *bot, float *ntop, float *nbot, 
         ++rot;
     }
     __syncthreads();
+  }
+  if (SEATS) {
+    if (act) {
+      int j = i + bs - 1;
+      if (j >= bs) j -= bs;
+      if (jacobi_pair_reg_out<GW, CW>(xv, al, bot + (size_t)j * a_pad, nbot + j,
+                                      rbot + (size_t)j * a_pad, rnbot + j, n4, tol2, lane, mask,
+                                      wred) &&
+          lane == 0)
+        ++rot;
+      float4 *xo = reinterpret_cast<float4 *>(rtop + (size_t)i * a_pad);
+#pragma unroll
+      for (int q = 0; q < CW; ++q) {
+        const int e4 = lane + GW * q;
+        if (e4 < n4) xo[e4] = xv[q];
+      }
+      if (lane == 0) rntop[i] = al;
+    }
+    return rot;
   }
   if (act) {
 #pragma unroll
@@ -565,6 +635,10 @@ __host__ __device__ constexpr int clu_max_threads(int gw, int cw) {
 // 256-thread bound (up to 255 registers, so fewer CTAs per SM).
 __host__ __device__ constexpr bool clu_has_reg(int gw, int cw) {
   return (gw == 16 && cw <= 3) || (gw == 8 && cw <= 8);
+}
+// REG variants whose registers also hold the last round's seats (no spills)
+__host__ __device__ constexpr bool clu_seats(int gw, int cw, bool reg) {
+  return reg && ((gw == 16 && cw <= 2) || (gw == 8 && cw <= 5));
 }
 __host__ __device__ constexpr int clu_bound(int gw, int cw, bool reg) {
   return (reg && gw == 8) ? 256 : clu_max_threads(gw, cw);
@@ -632,23 +706,38 @@ __global__ void __launch_bounds__(clu_bound(GW, CW, REG), 1) jacobi_cluster_kern
         __syncthreads();
         rot += intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
       }
-      if (REG && (int)(blockDim.x / GW) >= bs)
-        rot += cross_pass_reg<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
-      else
-        rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
-      // move the two blocks one seat along the circle (DSMEM copies)
+      // then move the two blocks one seat along the circle (DSMEM): stored into
+      // their next seats by the last round of the register pass where the
+      // registers allow it, else copied after the pass
       const int nxt = cur ^ 1;
+      const bool regpass = REG && (int)(blockDim.x / GW) >= bs;
+      if (clu_seats(GW, CW, REG) && regpass) {
+        rot += cross_pass_reg<GW, CW, clu_seats(GW, CW, REG)>(
+            top, bot, ntop, nbot, bs, a_pad, tol2, wred,
+            cl.map_shared_rank(slot(nxt, dst_top_tb), dst_top_rank),
+            cl.map_shared_rank(nslot(nxt, dst_top_tb), dst_top_rank),
+            cl.map_shared_rank(slot(nxt, dst_bot_tb), dst_bot_rank),
+            cl.map_shared_rank(nslot(nxt, dst_bot_tb), dst_bot_rank));
+      } else {
+        if (regpass)
+          rot += cross_pass_reg<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+        else
+          rot += cross_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
 #pragma unroll
-      for (int tb = 0; tb < 2; ++tb) {
-        const int dr = tb == 0 ? dst_top_rank : dst_bot_rank;
-        const int dtb = tb == 0 ? dst_top_tb : dst_bot_tb;
-        float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slot(nxt, dtb), dr));
-        const float4 *src = reinterpret_cast<const float4 *>(slot(cur, tb));
-        for (int idx = threadIdx.x; idx < blk_floats / 4; idx += blockDim.x) dst[idx] = src[idx];
-        float *dn = cl.map_shared_rank(nslot(nxt, dtb), dr);
-        const float *sn = nslot(cur, tb);
-        for (int i = threadIdx.x; i < bs; i += blockDim.x) dn[i] = sn[i];
-        if (threadIdx.x == 0) cl.map_shared_rank(&blk[0][0], dr)[nxt * 2 + dtb] = blk[cur][tb];
+        for (int tb = 0; tb < 2; ++tb) {
+          const int dr = tb == 0 ? dst_top_rank : dst_bot_rank;
+          const int dtb = tb == 0 ? dst_top_tb : dst_bot_tb;
+          float4 *dst = reinterpret_cast<float4 *>(cl.map_shared_rank(slot(nxt, dtb), dr));
+          const float4 *src = reinterpret_cast<const float4 *>(slot(cur, tb));
+          for (int idx = threadIdx.x; idx < blk_floats / 4; idx += blockDim.x) dst[idx] = src[idx];
+          float *dn = cl.map_shared_rank(nslot(nxt, dtb), dr);
+          const float *sn = nslot(cur, tb);
+          for (int i = threadIdx.x; i < bs; i += blockDim.x) dn[i] = sn[i];
+        }
+      }
+      if (threadIdx.x == 0) {
+        cl.map_shared_rank(&blk[0][0], dst_top_rank)[nxt * 2 + dst_top_tb] = blk[cur][0];
+        cl.map_shared_rank(&blk[0][0], dst_bot_rank)[nxt * 2 + dst_bot_tb] = blk[cur][1];
       }
       cl.sync();
       cur = nxt;
