@@ -136,7 +136,7 @@ __device__ __forceinline__ void tmem_accumulate(uint32_t tmem, int buf, int warp
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1) mode3_tc_kernel(
+__global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
     const float *__restrict__ Qm, int64_t sr, int64_t sc, const float *__restrict__ X,
     float *__restrict__ Y, int64_t P, int64_t S, int64_t N, const float *__restrict__ Aref,
     double *__restrict__ errp, double *__restrict__ xpart, double *__restrict__ ypart,
