@@ -15,12 +15,17 @@
 // registers (round to nearest) while the next chunk's MMAs run.
 //
 // Operands: the tensor is pixel-contiguous, i.e. MN-major for this product,
-// and M is tiny; both are streamed by the 128 threads of the CTA in chunks of
-// 32 along S (each thread's values for chunk c + 1 are requested while chunk c
-// is written and issued) and written into shared memory in the K-major,
+// and M is tiny; both are streamed in chunks of 32 along S and written into
+// shared memory in the K-major,
 // 128-byte-swizzled canonical layout (row = pixel or slice, 32 tf32 = 128 bytes per row, 8-row
-// atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  Each load of a
-// warp covers 32 consecutive pixels (coalesced).  Two
+// atoms of 1024 bytes, 16-byte chunk index XOR (row mod 8)).  The tensor's
+// chunks arrive either through the threads' registers (each thread's values
+// for chunk c + 1 are requested while chunk c is written and issued; each load
+// of a warp covers 32 consecutive pixels), or, for longer contractions whose
+// rows are 16-byte aligned, by TMA: 32 x 128 FP32 boxes of the S x N matrix
+// into a ring of TMA_STAGES raw stages, so that several chunks are in flight
+// per SM (out-of-range rows and pixels read as zero); the threads then convert
+// from shared memory.  Two
 // stages: while the MMAs of chunk c run, the threads fill chunk c+1; a stage
 // is refilled only after the tcgen05.commit of its previous MMAs has arrived
 // on that stage's mbarrier.  Every mbarrier wait is bounded; on expiry the
@@ -31,6 +36,11 @@
 // of TMEM lane r (tcgen05.ld), which they store as coalesced 128-byte rows of
 // Y, fusing the optional sums |Aref - Y|^2, |Y|^2 and |X|^2 (FP32 over a few
 // terms, FP64 beyond).
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "pp_internal.h"
 
 namespace pp {
@@ -40,6 +50,8 @@ constexpr int TM = 128;        // pixels per CTA (MMA M)
 constexpr int TK = 32;         // S per stage: one 128-byte swizzle row of tf32
 constexpr int THREADS = 256;   // two threads per pixel row (halves of K and of the columns)
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int TMA_STAGES = 4;                     // raw FP32 chunks in flight (TMA path)
+constexpr int RAW_BYTES = TK * TM * 4;            // one 32 x 128 FP32 box
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -104,6 +116,22 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
+               : "memory");
+}
+
+// one 2-D box of the tensor map at (x = pixel, y = S row) into shared memory,
+// completing `bytes` on the mbarrier
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+
 // bounded wait: false after ~WAIT_CYCLES
 __device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
   const long long t0 = clock64();
@@ -136,8 +164,12 @@ __device__ __forceinline__ void tmem_accumulate(uint32_t tmem, int buf, int warp
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
-    const float *__restrict__ Qm, int64_t sr, int64_t sc, const float *__restrict__ X,
+// TMA: chunks of X arrive by TMA through `tmap` (X's S x N matrix), else
+// through the threads' registers
+template <bool TMA>
+__global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
+    const __grid_constant__ CUtensorMap tmap, const float *__restrict__ Qm, int64_t sr,
+    int64_t sc, const float *__restrict__ X,
     float *__restrict__ Y, int64_t P, int64_t S, int64_t N, const float *__restrict__ Aref,
     double *__restrict__ errp, double *__restrict__ xpart, double *__restrict__ ypart,
     int32_t *status) {
@@ -149,6 +181,7 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[TMA_STAGES];   // TMA path: raw stage filled
   __shared__ uint32_t tmem_base_sh;
   __shared__ double red[THREADS / 32];
 
@@ -167,6 +200,9 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+    if (TMA)
+      for (int i = 0; i < TMA_STAGES; ++i)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[i])));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -182,6 +218,22 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
   const int nchunks = (int)((S + TK - 1) / TK);
   double xs = 0.0;
   bool ok = true;
+  // TMA path: raw FP32 stages after the two converted stages; chunk c goes to
+  // raw stage c % TMA_STAGES, and is refilled with chunk c + TMA_STAGES once
+  // every thread has converted it (the barrier before the MMA issue)
+  unsigned char *raw = smem + 2 * STAGE;
+  int issued = 0;                          // TMA boxes issued (thread 0)
+  auto tma_issue = [&](int c) {
+    const int rs = c % TMA_STAGES;
+    const uint32_t fb = smem_u32(&full[rs]);
+    mbar_expect_tx(fb, (uint32_t)RAW_BYTES);
+    tma_load_2d(smem_u32(raw + rs * RAW_BYTES), &tmap, (int)n0, c * TK, fb);
+    ++issued;
+  };
+  if (TMA && tid == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    for (int c = 0; c < nchunks && c < TMA_STAGES; ++c) tma_issue(c);
+  }
   // chunk c's operands are loaded into registers one iteration ahead, so the
   // global-memory latency overlaps the previous chunk's barrier and MMA issue
   const int64_t pix = n0 + row;
@@ -192,7 +244,7 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
 #pragma unroll
     for (int k = 0; k < TK / 2; ++k) {
       const int64_t s = s0 + khalf * (TK / 2) + k;
-      va[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
+      if (!TMA) va[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
       vb[k] = (row < NT && trow < P && s < S) ? Qm[trow * sr + s * sc] : 0.f;
     }
   };
@@ -205,6 +257,14 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
       if (__syncthreads_or(!ok)) { ok = false; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       tmem_accumulate(tmem, st, warp, acc);
+    }
+    if (TMA) {   // this chunk's raw stage: row s of the box is 128 pixels
+      const int rs = c % TMA_STAGES;
+      if (!mbar_wait(smem_u32(&full[rs]), (uint32_t)((c / TMA_STAGES) & 1))) ok = false;
+      if (__syncthreads_or(!ok)) { ok = false; break; }
+      const float *rp = reinterpret_cast<const float *>(raw + rs * RAW_BYTES);
+#pragma unroll
+      for (int k = 0; k < TK / 2; ++k) va[k] = rp[(khalf * (TK / 2) + k) * TM + row];
     }
     // ---- A: pixel row `row`, 16 values along S (this thread's half of the chunk)
     {
@@ -261,6 +321,16 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
         mma_tf32(d, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, 1u);
       }
       mma_commit(smem_u32(&mbar[st]));
+      if (TMA && c + TMA_STAGES < nchunks) tma_issue(c + TMA_STAGES);
+    }
+  }
+  // TMA path: on an early exit, let the boxes in flight land before the CTA
+  // (and its shared memory) goes away; every wait is bounded
+  if (TMA && tid == 0 && !ok) {
+    for (int c = 0; c < issued; ++c) {
+      // boxes below the failed chunk were consumed; the rest are waited here
+      if (!mbar_try(smem_u32(&full[c % TMA_STAGES]), (uint32_t)((c / TMA_STAGES) & 1)))
+        (void)mbar_wait(smem_u32(&full[c % TMA_STAGES]), (uint32_t)((c / TMA_STAGES) & 1));
     }
   }
   // the last two chunks
@@ -334,8 +404,44 @@ __global__ void __launch_bounds__(THREADS, 2) mode3_tc_kernel(
   }
 }
 
-size_t tc_smem() {
-  return (size_t)2 * (2 * TM * 128 + 2 * NT * 128) + 1024;   // 2 stages + alignment slack
+size_t tc_smem(bool tma) {
+  // 2 converted stages (+ the TMA ring) + alignment slack
+  return (size_t)2 * (2 * TM * 128 + 2 * NT * 128) + (tma ? (size_t)TMA_STAGES * RAW_BYTES : 0) +
+         1024;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// The S x N FP32 matrix X as a TMA map with 32 x 128 boxes; false when X's
+// rows are not 16-byte aligned or the driver refuses
+bool make_x_map(const float *X, int64_t S, int64_t N, CUtensorMap *map) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || N % 4 != 0) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)S};
+  const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)TM, (cuuint32_t)TK};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
@@ -350,14 +456,19 @@ cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float
                             int32_t *status, cudaStream_t st) {
   if (n_partials) *n_partials = (int)(((N + TM - 1) / TM) * ((P + NT - 1) / NT));
   if (n_xpart) *n_xpart = (int)((N + TM - 1) / TM);
-  const size_t smem = tc_smem();
-  cudaError_t e = cudaFuncSetAttribute(mode3_tc_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // TMA for contractions of more than two chunks (two CTAs per SM otherwise)
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const bool tma = S > 2 * TK && make_x_map(X, S, N, &map);
+  const size_t smem = tc_smem(tma);
+  auto kern = tma ? mode3_tc_kernel<true> : mode3_tc_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), 1);
   count_launch(1);
-  mode3_tc_kernel<<<grid, THREADS, smem, st>>>(Qm, sr, sc, X, Y, P, S, N, Aref, errp, xpart,
-                                               ypart, status);
+  kern<<<grid, THREADS, smem, st>>>(map, Qm, sr, sc, X, Y, P, S, N, Aref, errp, xpart, ypart,
+                                    status);
   return cudaGetLastError();
 }
 
