@@ -57,10 +57,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// x rounded to the nearest tf32 value (10 stored mantissa bits), ties away
+// from zero, in the FP32 container: half a tf32 ulp is added to the magnitude
+// bits and the 13 bits tf32 drops are cleared (a carry into the exponent is the
+// correct rounding up).  Integer ALU work, unlike the conversion pipe; the same
+// value as the PTX cvt.rna.tf32.f32 for every finite x.
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // byte offset of element (row, k), k < 32, in a K-major SW128 tile
@@ -313,12 +316,16 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
       const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
       const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
       const uint32_t d = tmem + (uint32_t)(st * NT);
+      // the descriptors' address field is (address >> 4) and every address here
+      // is below 256 KB, so a K step of 32 bytes adds 2 to each descriptor
+      const uint64_t dah = sw128_desc(a_hi), dal = sw128_desc(a_lo);
+      const uint64_t dbh = sw128_desc(b_hi), dbl = sw128_desc(b_lo);
 #pragma unroll
       for (int kk = 0; kk < TK / 8; ++kk) {   // 8 tf32 = 32 bytes of K per MMA
-        const uint32_t o = 32u * kk;
-        mma_tf32(d, sw128_desc(a_lo + o), sw128_desc(b_hi + o), IDESC, kk > 0 ? 1u : 0u);
-        mma_tf32(d, sw128_desc(a_hi + o), sw128_desc(b_lo + o), IDESC, 1u);
-        mma_tf32(d, sw128_desc(a_hi + o), sw128_desc(b_hi + o), IDESC, 1u);
+        const uint64_t o = 2u * (uint32_t)kk;
+        mma_tf32(d, dal + o, dbh + o, IDESC, kk > 0 ? 1u : 0u);
+        mma_tf32(d, dah + o, dbl + o, IDESC, 1u);
+        mma_tf32(d, dah + o, dbh + o, IDESC, 1u);
       }
       mma_commit(smem_u32(&mbar[st]));
       if (TMA && c + TMA_STAGES < nchunks) tma_issue(c + TMA_STAGES);
