@@ -226,13 +226,16 @@ def _tsvdqII_case(A, Q, gamma, **opts):
 
 @pytest.mark.parametrize("precond", [True, False])
 @pytest.mark.parametrize("shape", [(40, 23, 57), (40, 57, 23), (24, 33, 33), (64, 130, 9),
-                                   (16, 37, 300), (14, 130, 176)])
+                                   (16, 37, 300), (14, 130, 176), (12, 128, 176), (12, 176, 128),
+                                   (12, 100, 177)])
 def test_tsvdqII_with_and_without_qr_preconditioner(shape, precond):
     """Both Jacobi paths (rows of R from the QR with column pivoting, or the
     slice itself) against the oracle, on wide, tall, square and very flat slices.
-    The first four (and the video-shaped slices) take the register-resident QR;
-    37 x 300 (vectors longer than 176) and 130 x 176 (more than 128 vectors)
-    take the shared-memory QR."""
+    The first four (and the video-shaped slices) take the register-resident QR,
+    128 x 176 and 176 x 128 at its largest shape (128 vectors of 176 entries,
+    11 float4 per lane); 37 x 300 (vectors longer than 176), 100 x 177 (just
+    past that bound) and 130 x 176 (more than 128 vectors) take the
+    shared-memory QR."""
     n, l, m = shape
     A = inputs.gaussian(shape, seed=31 + l)
     Q = inputs.random_q(n, 12, seed=32)
