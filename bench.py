@@ -255,6 +255,23 @@ def timed_steps(run, steps, warmup, torch, flush, stream, stage_events=None):
     return times, stage_ms
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks: the job takes as long as its slowest rank
+    (x itself with one process)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, steps, total_ms):
+    """Whole-job entries/s: every rank processes its own tensor of the workload
+    each step (weak scaling), in the slowest rank's time."""
+    return world * L * M * N * steps / (total_ms / 1e3)
+
+
 def run_ours(args):
     import torch
 
@@ -323,13 +340,9 @@ def run_ours(args):
     if rep.status != 0:
         raise RuntimeError(f"device status {binding.status_str(rep.status)}")
 
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dist, dev)
     ms_per_step = total_ms / args.steps
-    value = world * L * M * N * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, total_ms)
 
     # ---------------- dominant kernel roofline (Jacobi SVD, stage 1 -> 2)
     peaks, peak_kind = load_peaks()
@@ -614,16 +627,14 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
     finish(n_steps - 1)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s, serial_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s, serial_s = float(t[0].item()), float(t[1].item())
-    return {"value": world * L * M * N * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    serial_s = max_over_ranks(serial_s, dist, dev)
+    return {"value": job_throughput(world, args.steps, 1e3 * e2e_s), "unit": UNIT,
             "h2d_bytes_per_step": int(A.nbytes + Qp.nbytes),
             "d2h_bytes_per_step": int(statistics.mean(moved[:args.steps])),
             "ms_per_step": 1e3 * e2e_s / args.steps,
             "pipelined": "two buffer sets; inputs in on a copy stream while the previous step computes",
-            "serial": {"value": world * L * M * N * args.steps / serial_s,
+            "serial": {"value": job_throughput(world, args.steps, 1e3 * serial_s),
                        "ms_per_step": 1e3 * serial_s / args.steps}}
 
 
