@@ -361,7 +361,9 @@ template <int NCH>
 __global__ void __launch_bounds__(QR_THREADS) qrcp_reg_kernel(QrArgs A) {
   extern __shared__ __align__(16) float qs[];
   constexpr int NW = QR_THREADS / 32;
-  __shared__ unsigned cand_v[2][NW], cand_j[2][NW], cand_g[2][NW];
+  // candidates: trailing norm and key = vector << 8 | group that published it
+  // (the smallest key among equal norms is the lowest vector index)
+  __shared__ unsigned cand_v[2][NW], cand_j[2][NW];
   __shared__ int move_j[2];
   const int64_t f = blockIdx.x;
   const int l = (int)A.l, m = (int)A.m;
@@ -411,12 +413,12 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_reg_kernel(QrArgs A) {
 #pragma unroll
     for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
     unsigned bv, bj;
-    warp_pivot(s, live ? (unsigned)g : QR_NONE, bv, bj);
-    if (live && (unsigned)g == bj) qr_reg_store<NCH>(cvec + (size_t)warp * QR_REG_A4, v, glane, a4);
+    const unsigned key = ((unsigned)g << 8) | (unsigned)g;   // group == vector before any hand-over
+    warp_pivot(s, live ? key : QR_NONE, bv, bj);
+    if (live && key == bj) qr_reg_store<NCH>(cvec + (size_t)warp * QR_REG_A4, v, glane, a4);
     if (lane == 0) {
       cand_v[0][warp] = bv;
       cand_j[0][warp] = bj;
-      cand_g[0][warp] = bj;           // group == vector before any hand-over
     }
   }
   __syncthreads();
@@ -434,11 +436,11 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_reg_kernel(QrArgs A) {
     const unsigned cj = has ? cand_j[par][lane] : QR_NONE;
     unsigned bv, bj;
     warp_pivot(has ? __uint_as_float(cand_v[par][lane]) : 0.f, cj, bv, bj);
-    const unsigned hit = __ballot_sync(0xffffffffu, has && cj == bj && bj != QR_NONE);
-    const int wi = hit ? __ffs(hit) - 1 : 0;
-    const int sp = bj < (unsigned)b ? (int)bj : 0;
-    int gs = (int)cand_g[par][wi];    // group that published the pivot ...
-    if (gs == gl_prev) gs = gs_prev;  // ... unless it has handed it over since
+    const bool found = bj != QR_NONE;
+    const int sp = found ? (int)(bj >> 8) : 0;
+    int gs = found ? (int)(bj & 255u) : 0;   // group that published the pivot ...
+    const int wi = gs / (32 / QG);           // (its warp's candidate slot)
+    if (gs == gl_prev) gs = gs_prev;         // ... unless it has handed it over since
     const float4 *p4 = cvec + ((size_t)par * NW + wi) * QR_REG_A4;
     const float *pf = reinterpret_cast<const float *>(p4);
     const float x0 = pf[k];
@@ -471,16 +473,14 @@ __global__ void __launch_bounds__(QR_THREADS) qrcp_reg_kernel(QrArgs A) {
     float s = (s4.x + s4.y) + (s4.z + s4.w);
 #pragma unroll
     for (int o = QG / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, QG);
-    warp_pivot(s, live ? (unsigned)myj : QR_NONE, bv, bj);
-    if (live && (unsigned)myj == bj)
+    const unsigned mykey = ((unsigned)myj << 8) | (unsigned)g;
+    warp_pivot(s, live ? mykey : QR_NONE, bv, bj);
+    if (live && mykey == bj)
       qr_reg_store<NCH>(cvec + ((size_t)(par ^ 1) * NW + warp) * QR_REG_A4, v, glane, a4);
     if (lane == 0) {
       cand_v[par ^ 1][warp] = bv;
       cand_j[par ^ 1][warp] = bj;
     }
-    // the warp's candidate group (the one whose vector won the warp)
-    const unsigned won = __ballot_sync(0xffffffffu, live && (unsigned)myj == bj);
-    if (lane == 0 && won) cand_g[par ^ 1][warp] = (unsigned)(warp * (32 / QG) + (__ffs(won) - 1) / QG);
     // hand the last live group's vector to the pivot's group
     const int gl = b - k - 1;
     if (gl != gs && g == gl) {
