@@ -51,6 +51,7 @@ constexpr int64_t MAX_LONG_SIDE = 768;   // longest slice side the Jacobi kernel
 struct DecompWs {
   float *Ah, *W, *sig, *Ahk;
   int32_t *perm, *sweeps, *status, *rank;
+  int32_t *jaux;       // device-wide Jacobi kernel's counters (jacobi_aux_bytes)
   double *kept_p, *disc_p, *part_a, *part_h, *part_e, *scal, *keys;
   int64_t *K;
   // QR preconditioner of the Jacobi SVD (slices that fit its shared memory)
@@ -83,6 +84,7 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
   w.part_e = c.take<double>(pp::mode3_tc_partials(n, l * m));
   w.scal = c.take<double>(8);
   w.status = c.take<int32_t>(1);
+  w.jaux = c.take<int32_t>((int64_t)pp::jacobi_aux_bytes(p) / 4);
   w.K = c.take<int64_t>(1);
   if (ragged) {
     w.keys = c.take<double>(p * b);
@@ -116,7 +118,7 @@ struct HosvdWs {
   float *Uk, *sk, *Vk;                       // *Q-SVD factors at k = min(k1, k2)
   float *gpart, *G1, *G2;                    // Gram partials and the two Grams
   float *Wg, *sigg;                          // Jacobi of a Gram matrix (one slice)
-  int32_t *permg, *sweepsg;
+  int32_t *permg, *sweepsg, *jauxg;
   float *U1, *s1, *V1, *U2, *s2, *V2;        // leading eigenvectors (V1, V2 are used)
   float *P1, *P2, *T;                        // projectors and the slice-wise temporary
 };
@@ -137,6 +139,7 @@ HosvdWs carve_hosvd(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, int64_
   h.sigg = c.take<float>(d);
   h.permg = c.take<int32_t>(d);
   h.sweepsg = c.take<int32_t>(1);
+  h.jauxg = c.take<int32_t>((int64_t)pp::jacobi_aux_bytes(1) / 4);
   h.U1 = c.take<float>(l * k1);
   h.s1 = c.take<float>(k1);
   h.V1 = c.take<float>(l * k1);
@@ -175,7 +178,7 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
 
 struct U3Ws {
   float *part, *G, *W, *sig, *Uh, *s, *Vh;
-  int32_t *perm, *sweeps, *status;
+  int32_t *perm, *sweeps, *status, *jaux;
 };
 
 U3Ws carve_u3(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p) {
@@ -190,6 +193,7 @@ U3Ws carve_u3(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p) {
   w.perm = c.take<int32_t>(n);
   w.sweeps = c.take<int32_t>(1);
   w.status = c.take<int32_t>(1);
+  w.jaux = c.take<int32_t>((int64_t)pp::jacobi_aux_bytes(1) / 4);
   return w;
 }
 
@@ -236,6 +240,7 @@ pp_status check_ws(const void *ws, size_t ws_bytes, size_t need) {
 
 struct Opts {
   int32_t max_sweeps = 30;
+  bool allow_grid = true;   // false inside tsvdqII_batched (concurrent launches)
   int32_t check_q = 0;
   float q_tol = 1e-5f;
   int32_t check_finite = 0;
@@ -243,8 +248,18 @@ struct Opts {
   int32_t precond = 0;
 };
 
+// Set while tsvdqII_batched enqueues its items on several streams: their
+// Jacobi launches may run at the same time, which the device-wide cooperative
+// Jacobi kernel (all its CTAs resident at once, waiting on each other) must not.
+thread_local bool t_concurrent = false;
+struct ConcurrentScope {
+  ConcurrentScope() { t_concurrent = true; }
+  ~ConcurrentScope() { t_concurrent = false; }
+};
+
 Opts read_opts(const pp_opts *o) {
   Opts r;
+  r.allow_grid = !t_concurrent;
   if (o) {
     if (o->max_sweeps > 0) r.max_sweeps = o->max_sweeps;
     r.check_q = o->check_q;
@@ -299,6 +314,8 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   ja.key_l = l;
   ja.key_m = m;
   ja.max_sweeps = o.max_sweeps;
+  ja.aux = w.jaux;
+  ja.allow_grid = o.allow_grid;
   if (w.pc) {
     const int64_t b = l < m ? l : m;
     pp::QrArgs qa{w.Ah, w.R, w.qperm, l, m, p};
@@ -786,6 +803,7 @@ pp_status tsvdqII_batched(const pp_batch_item *items, int64_t count, double gamm
   std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
     return items[x].l * items[x].m * items[x].n > items[y].l * items[y].m * items[y].n;
   });
+  ConcurrentScope concurrent;
   for (int64_t i = 0; i < count; ++i) {
     const pp_batch_item &it = items[order[(size_t)i]];
     if (pp_status e = tsvdqII(it.A, it.Q, it.l, it.m, it.n, it.p, gamma, it.rho, it.offs,
@@ -845,6 +863,8 @@ pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m, in
     ja.m = d;
     ja.p = 1;
     ja.max_sweeps = o.max_sweeps;
+    ja.aux = h.jauxg;
+    ja.allow_grid = o.allow_grid;
     ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(d, d);
     PP_TRY(pp::launch_jacobi(ja, st));
     pp::FactorArgs fg;
@@ -924,6 +944,8 @@ pp_status pprod_u3(const float *A, int64_t l, int64_t m, int64_t n, int64_t p, f
   ja.m = n;
   ja.p = 1;
   ja.max_sweeps = o.max_sweeps;
+  ja.aux = w.jaux;
+  ja.allow_grid = o.allow_grid;
   ja.tol = o.jacobi_tol > 0.f ? o.jacobi_tol : default_tol(n, n);
   PP_TRY(pp::launch_jacobi(ja, st));
   // leading p: the long-side (normalised rotated) vectors, orthonormal to working accuracy

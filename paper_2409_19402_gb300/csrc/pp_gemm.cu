@@ -22,7 +22,6 @@ constexpr int BM = 64;   // output slices per CTA
 constexpr int BN = 128;  // pixels per CTA
 constexpr int BK = 16;   // contraction step
 constexpr int NT = 256;  // threads per CTA
-constexpr int64_t NUM_SMS_GEMM = 152;
 
 __device__ __forceinline__ double block_sum_double(double v, double *red) {
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -246,7 +245,7 @@ __global__ void stiefel_kernel(const float *__restrict__ Q, const float *__restr
 
 int64_t nt_splits(int64_t R, int64_t S, int64_t K) {
   const int64_t tiles = ((R + 63) / 64) * ((S + 63) / 64);
-  int64_t z = (NUM_SMS_GEMM * 3 + tiles - 1) / tiles;
+  int64_t z = ((int64_t)num_sms() * 3 + tiles - 1) / tiles;
   const int64_t zmax = (K + 255) / 256;   // at least 256 of K per split
   if (z > zmax) z = zmax;
   return z < 1 ? 1 : z;

@@ -12,6 +12,12 @@ namespace pp {
 // Count `n` kernel launches in the process-wide counter (pp_kernel_launches).
 void count_launch(int n);
 
+// Number of SMs of the current device (cudaDevAttrMultiProcessorCount, cached
+// per device; 152 if the query fails).  Grids that fill the device and the
+// launch-shape cost model use it; buffers sized from it are sized for the
+// device that is current when the size is asked for.
+int num_sms();
+
 // Round x up to a multiple of a.
 static inline int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
@@ -77,8 +83,16 @@ struct JacobiArgs {
   int32_t max_sweeps = 30;
   float tol = 0.f;            // rotation threshold on |cos|
   int64_t key_l = 0, key_m = 0;   // slice shape for registered launch shapes (0: l, m)
+  // jacobi_aux_bytes(p) of workspace for the device-wide kernel that takes
+  // slices too large for one CTA's shared memory; nullptr (or allow_grid =
+  // false, e.g. for launches that run concurrently with other Jacobi launches)
+  // keeps such slices on the single-CTA block-cyclic kernel
+  int32_t *aux = nullptr;
+  bool allow_grid = true;
 };
 int64_t jacobi_apad(int64_t l, int64_t m);
+size_t jacobi_aux_bytes(int64_t p);
+constexpr int JACOBI_GRID_MAX_SWEEPS = 64;   // sweep cap of the device-wide kernel
 // register (C >= 1) or remove (C = 0) the Jacobi launch shape for l x m slices, p of them
 bool set_jacobi_shape(int64_t l, int64_t m, int64_t p, int C, int GW);
 cudaError_t launch_jacobi(const JacobiArgs &a, cudaStream_t st);

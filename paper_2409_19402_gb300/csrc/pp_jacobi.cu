@@ -779,7 +779,237 @@ int pick_group(int64_t a) {
   return 32;
 }
 
-constexpr int NUM_SMS = 152;
+// ------------------------------------------------------------------ grid kernel
+// Slices too large for one CTA's shared memory (e.g. 512 x 512), spread over
+// the whole device.  The b vectors of a slice are cut into nb (even) blocks of
+// bs vectors; a sweep is nb-1 block rounds of the round-robin circle over
+// blocks, and the nb/2 block pairs of a round -- of every slice -- are
+// independent work items, taken by the CTAs of one persistent cooperative
+// launch in turn.  An item loads its two blocks from W (global memory, L2
+// resident) into shared memory, computes their squared norms, orthogonalises
+// every cross pair of the two blocks (bs rounds of bs disjoint pairs, one pair
+// per group of GW lanes; the first block round of a sweep also covers the
+// pairs inside each block) and stores the blocks back.  A bounded grid
+// barrier separates block rounds.  Each item adds its rotation count to a
+// per-slice, per-sweep counter; a slice whose sweep rotated nothing is done
+// (every CTA reads the same counters after the barrier, so every CTA takes the
+// same decisions).  The pair arithmetic is that of the cluster kernel.
+//
+// aux (global, zeroed before the launch): [0] barrier arrivals, [1] barrier
+// generation, [2] abort flag, [8 ...] counters cnt[sweep * p + slice].
+constexpr long long GRID_WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz per barrier
+constexpr int GRID_AUX_HEAD = 8;
+
+// Bounded barrier over all CTAs of a cooperative launch.  false: the wait
+// expired here or in another CTA (PP_ETIMEOUT recorded); the caller returns.
+__device__ bool grid_barrier(int32_t *aux, int32_t *status, int *flag_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned *cnt = reinterpret_cast<unsigned *>(aux);
+    volatile unsigned *gen = reinterpret_cast<volatile unsigned *>(aux + 1);
+    volatile int32_t *abort_flag = aux + 2;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(cnt, 1u) == gridDim.x - 1) {
+      atomicExch(cnt, 0u);
+      __threadfence();
+      atomicAdd(reinterpret_cast<unsigned *>(aux + 1), 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (*abort_flag || clock64() - t0 > GRID_WAIT_CYCLES) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    if (!ok) {
+      aux[2] = 1;
+      set_status(status, PP_ETIMEOUT);
+    }
+    *flag_sh = ok;
+  }
+  __syncthreads();
+  return *flag_sh != 0;
+}
+
+// the two passes of a block-pair item, kept out of line so that each has the
+// kernel's registers to itself (inlined together they spill)
+template <int GW, int CW>
+__device__ __noinline__ int grid_intra(float *top, float *bot, float *ntop, float *nbot, int bs,
+                                       int a_pad, float tol2, float *wred) {
+  return intra_pass_warp<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+}
+template <int GW, int CW>
+__device__ __noinline__ int grid_cross(float *top, float *bot, float *ntop, float *nbot, int bs,
+                                       int a_pad, float tol2, float *wred) {
+  return cross_pass_reg<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+}
+
+constexpr int GRID_MAX_P = 4096;   // slices the device-wide kernel takes (activity flags)
+
+// THREADS = bs * GW: one group of GW lanes per cross pair of a round
+template <int GW, int CW, int THREADS>
+__global__ void __launch_bounds__(THREADS, 512 / THREADS) jacobi_grid_kernel(JacobiArgs A,
+                                                                             int a_pad, int bs,
+                                                                             int nb) {
+  extern __shared__ __align__(16) float sm[];   // top block | bottom block | 2 bs norms
+  __shared__ __align__(16) float red_scratch[THREADS];
+  __shared__ int flag_sh, rot_sh, any_sh;
+  __shared__ unsigned char active[GRID_MAX_P];   // slice still iterating in this sweep
+  float *wred = red_scratch + (threadIdx.x & ~31);
+  const int l = (int)A.l, m = (int)A.m;
+  const bool rows = l <= m;
+  const int b = rows ? l : m, a = rows ? m : l;
+  const int n4 = a_pad / 4;
+  const int64_t p = A.p;
+  const float tol2 = A.tol * A.tol;
+  int32_t *aux = A.aux;
+  int32_t *cnt = aux + GRID_AUX_HEAD;
+  float *top = sm, *bot = sm + (size_t)bs * a_pad;
+  float *ntop = sm + (size_t)2 * bs * a_pad, *nbot = ntop + bs;
+
+  // W <- the slices' vectors (rows, or columns when l > m), zero padded
+  const int64_t total = p * b * (int64_t)a_pad;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = idx / ((int64_t)b * a_pad);
+    const int64_t r = idx % ((int64_t)b * a_pad);
+    const int j = (int)(r / a_pad), e = (int)(r % a_pad);
+    const float *Xf = A.X + f * (int64_t)l * m;
+    A.W[idx] = e < a ? (rows ? Xf[(int64_t)j * m + e] : Xf[(int64_t)e * m + j]) : 0.f;
+  }
+  for (int64_t f = threadIdx.x; f < p; f += blockDim.x) active[f] = 1;
+  if (!grid_barrier(aux, A.status, &flag_sh)) return;
+
+  const int64_t items = p * (nb / 2);
+  int s = 0;
+  for (; s < A.max_sweeps; ++s) {
+    // a slice whose previous sweep rotated nothing is done (the counters of
+    // the earlier sweeps are final here, and the same for every CTA)
+    if (threadIdx.x == 0) any_sh = 0;
+    __syncthreads();
+    for (int64_t f = threadIdx.x; f < p; f += blockDim.x) {
+      if (s > 0 && active[f] && ((volatile const int32_t *)cnt)[(int64_t)(s - 1) * p + f] == 0)
+        active[f] = 0;
+      if (active[f]) any_sh = 1;
+    }
+    __syncthreads();
+    if (!any_sh) break;
+    for (int br = 0; br < nb - 1; ++br) {
+      for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t f = it / (nb / 2);
+        const int q = (int)(it % (nb / 2));
+        if (!active[f]) continue;   // uniform across the CTA
+        int I, J;
+        circle_pair(nb, br, q, I, J);
+        float4 *W4 = reinterpret_cast<float4 *>(A.W + f * (int64_t)b * a_pad);
+        for (int idx = threadIdx.x; idx < 2 * bs * n4; idx += blockDim.x) {
+          const int row = idx / n4, e4 = idx % n4;
+          const int v = row < bs ? I * bs + row : J * bs + (row - bs);
+          reinterpret_cast<float4 *>(sm)[idx] =
+              v < b ? W4[(int64_t)v * n4 + e4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        block_norms(top, ntop, bs, n4);
+        block_norms(bot, nbot, bs, n4);
+        __syncthreads();
+        int rot = 0;
+        if (br == 0) rot += grid_intra<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+        rot += grid_cross<GW, CW>(top, bot, ntop, nbot, bs, a_pad, tol2, wred);
+        for (int idx = threadIdx.x; idx < 2 * bs * n4; idx += blockDim.x) {
+          const int row = idx / n4, e4 = idx % n4;
+          const int v = row < bs ? I * bs + row : J * bs + (row - bs);
+          if (v < b) W4[(int64_t)v * n4 + e4] = reinterpret_cast<const float4 *>(sm)[idx];
+        }
+        if (threadIdx.x == 0) rot_sh = 0;
+        __syncthreads();
+        if (rot) atomicAdd(&rot_sh, rot);
+        __syncthreads();
+        if (threadIdx.x == 0 && rot_sh) atomicAdd(&cnt[(int64_t)s * p + f], rot_sh);
+      }
+      if (!grid_barrier(aux, A.status, &flag_sh)) return;
+    }
+  }
+  // singular values, order and sweep counts, one slice per CTA in turn
+  for (int64_t f = blockIdx.x; f < p; f += gridDim.x) {
+    int sw = 0;
+    while (sw < s && ((volatile const int32_t *)cnt)[(int64_t)sw * p + f] != 0) ++sw;
+    const bool conv = sw < s;
+    finish_slice(A.W + f * (int64_t)b * a_pad, b, a_pad, A.sig + f * b, A.perm + f * b, sm);
+    if (threadIdx.x == 0) {
+      A.sweeps[f] = conv ? sw + 1 : s;
+      if (!conv) set_status(A.status, PP_ENOCONV);
+    }
+    __syncthreads();
+  }
+}
+
+// Grid-kernel launch shape: one warp per pair, bs = 16 vectors per block (at
+// most half the vectors), 512 threads (one group per block vector in a cross
+// round; the top block held in registers across the cross pass).
+struct GridCfg {
+  int GW = 0, CW = 0, bs = 0, nb = 0, grid = 0, threads = 0;
+  size_t smem = 0;
+};
+
+template <int GW, int CW, int THREADS>
+cudaError_t grid_launch(const JacobiArgs &A, int a_pad, GridCfg &g, cudaStream_t st) {
+  auto kern = jacobi_grid_kernel<GW, CW, THREADS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)g.smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, g.smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t items = A.p * (g.nb / 2);
+  const int64_t cap = (int64_t)per_sm * num_sms();
+  g.grid = (int)(items < cap ? items : cap);
+  if (g.grid < 1) g.grid = 1;
+  e = cudaMemsetAsync(A.aux, 0, jacobi_aux_bytes(A.p), st);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)g.grid, 1, 1);
+  cfg.blockDim = dim3(THREADS, 1, 1);
+  cfg.dynamicSmemBytes = g.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch(1);
+  JacobiArgs Ac = A;
+  if (Ac.max_sweeps > JACOBI_GRID_MAX_SWEEPS) Ac.max_sweeps = JACOBI_GRID_MAX_SWEEPS;
+  return cudaLaunchKernelEx(&cfg, kern, Ac, a_pad, g.bs, g.nb);
+}
+
+cudaError_t launch_grid_jacobi(const JacobiArgs &A, int a_pad, cudaStream_t st) {
+  const int64_t a = A.l > A.m ? A.l : A.m;
+  const int64_t b = A.l < A.m ? A.l : A.m;
+  (void)a;
+  GridCfg g;
+  const int n4 = a_pad / 4;
+  if (A.p > GRID_MAX_P) return cudaErrorInvalidValue;
+  g.GW = 32;
+  g.CW = n4 <= 128 ? 4 : 6;
+  if (n4 > g.GW * g.CW) return cudaErrorInvalidValue;
+  g.bs = 16;
+  if (g.bs > (b + 1) / 2) g.bs = (int)((b + 1) / 2);
+  g.nb = (int)((b + g.bs - 1) / g.bs);
+  g.nb += g.nb & 1;
+  g.smem = (size_t)2 * g.bs * a_pad * sizeof(float) + (size_t)2 * g.bs * sizeof(float);
+  if ((int64_t)g.smem < b * 4) g.smem = (size_t)b * 4;   // finish_slice: b norms
+  // the cross pass needs one group per block vector: THREADS / GW >= bs
+  return g.CW == 4 ? grid_launch<32, 4, 512>(A, a_pad, g, st)
+                   : grid_launch<32, 6, 512>(A, a_pad, g, st);
+}
+
+
 constexpr int MAX_CLUSTER = 8;
 
 // registered launch shapes (pp_set_jacobi_shape): (l, m, p) -> (C, GW)
@@ -965,6 +1195,10 @@ bool set_jacobi_shape(int64_t l, int64_t m, int64_t p, int C, int GW) {
   return true;
 }
 
+size_t jacobi_aux_bytes(int64_t p) {
+  return (size_t)(GRID_AUX_HEAD + (int64_t)JACOBI_GRID_MAX_SWEEPS * p) * sizeof(int32_t);
+}
+
 int64_t jacobi_apad(int64_t l, int64_t m) {
   const int64_t a = l > m ? l : m;
   const int G = pick_group(a);
@@ -1000,7 +1234,7 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
     }
     cudaGetLastError();
   }
-  if (regC < 0 && A.p < NUM_SMS / 2) {
+  if (regC < 0 && A.p < num_sms() / 2) {
     ClusterCfg cc;
     if (pick_cluster(A, a_pad, cc)) {
       if (log)
@@ -1010,6 +1244,15 @@ cudaError_t launch_jacobi(const JacobiArgs &A, cudaStream_t st) {
                 cc.max_clusters);
       return launch(A, a_pad, cc, st);
     }
+  }
+  // slices too large for one CTA's shared memory: the device-wide kernel
+  if (b * row_bytes > SMEM_BUDGET && A.aux && A.allow_grid) {
+    const cudaError_t e = launch_grid_jacobi(A, a_pad, st);
+    if (log)
+      fprintf(stderr, "[pprod] jacobi grid: p=%lld a_pad=%d -> %s\n", (long long)A.p, a_pad,
+              cudaGetErrorString(e));
+    if (e == cudaSuccess) return e;
+    cudaGetLastError();
   }
   if (log) fprintf(stderr, "[pprod] jacobi single-CTA: p=%lld a_pad=%d\n", (long long)A.p, a_pad);
   int bs;                // block size in vectors; bs >= b means resident

@@ -19,13 +19,17 @@
 // same scratch and race: order them on one stream or with events.
 //
 // Host code cannot use the array's name as a device address (in host code it
-// names a host-side stand-in).  The first call made on each device, with that
-// device current, asks the runtime for the array's device address with
-// cudaGetSymbolAddress and caches it; that first call may load the module and
-// should therefore come before any other work that must not be disturbed, in
-// particular before any stream capture.  No call allocates or frees memory.
-#include <mutex>
-
+// names a host-side stand-in).  Every call, with the target device current,
+// asks the runtime for the array's device address with cudaGetSymbolAddress
+// (cheap once the module is loaded; nothing is cached, so a context torn down
+// and recreated, e.g. after cudaDeviceReset, gets the new address).  The first
+// call on a device may load the module and should therefore come before any
+// other work that must not be disturbed, in particular before any stream
+// capture.  No call allocates or frees memory.
+//
+// Argument checks run in tsvdqII's own order (pointers, gamma, sizes, the
+// longest slice side) before the size of the scratch is compared, so a bad
+// argument gets the same status from both entry points.
 #include "pp_internal.h"
 
 namespace {
@@ -33,21 +37,11 @@ namespace {
 // The scratch.  256-byte aligned, as the workspace contract of pprod.h asks.
 static __device__ __align__(256) unsigned char pp_noalloc_scratch[PP_NOALLOC_SCRATCH_BYTES];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[MAX_DEVICES] = {};
-
 // Device address of the scratch on the current device (nullptr on failure).
 void *scratch_address() {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return nullptr;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, pp_noalloc_scratch) != cudaSuccess || !ptr) return nullptr;
-    g_scratch_ptr[dev] = ptr;
-  }
-  return g_scratch_ptr[dev];
+  void *ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, pp_noalloc_scratch) != cudaSuccess) return nullptr;
+  return ptr;
 }
 
 }  // namespace
@@ -57,10 +51,14 @@ extern "C" pp_status tsvdqII_noalloc(const float *A, const float *Q, int64_t l, 
                                      int64_t *offs, float *Uh_pk, float *s_pk, float *Vh_pk,
                                      float *Ak, pp_report *rep, const pp_opts *opts,
                                      void *stream) {
-  if (l < 1 || m < 1 || n < 1 || p < 1 || p > n) return PP_ESHAPE;
+  // tsvdqII without a workspace runs every one of its argument checks and then
+  // stops at the workspace check (PP_EWORKSPACE), enqueuing nothing; any other
+  // status is an argument error, reported as tsvdqII reports it.
+  const pp_status pre = tsvdqII(A, Q, l, m, n, p, gamma, rho, offs, Uh_pk, s_pk, Vh_pk, Ak, rep,
+                                opts, nullptr, 0, stream);
+  if (pre != PP_EWORKSPACE) return pre;
   pp_shape sh{l, m, n, p, 0, 0};
   const size_t need = pp_workspace_bytes(PP_OP_TSVDQII, &sh);
-  if (need == 0) return PP_ESHAPE;
   if (need > (size_t)PP_NOALLOC_SCRATCH_BYTES) return PP_EWORKSPACE;   // beyond the maximum
   void *ws = scratch_address();
   if (!ws) return PP_ECUDA;

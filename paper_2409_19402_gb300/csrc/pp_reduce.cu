@@ -2,13 +2,21 @@
 // |A|_F^2 and |A-hat|_F^2), input checks (Q^T Q = I for Q in St_{n,p}, finite
 // input) and the device-written report.  Every reduction runs on a fixed grid
 // with a fixed combination order, so results are bitwise reproducible.
+#include <atomic>
+
 #include "pp_internal.h"
 
 namespace pp {
 namespace {
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_MAX_BLOCKS = 2048;   // bound of the partial-sum buffers
 constexpr int RED_THREADS = 256;
+
+// two CTAs per SM, within the partial-buffer bound
+int red_blocks() {
+  const int b = 2 * num_sms();
+  return b < RED_MAX_BLOCKS ? b : RED_MAX_BLOCKS;
+}
 
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[32];
@@ -129,7 +137,23 @@ __global__ void hosvd_report_kernel(HosvdReportArgs a) {
 
 }  // namespace
 
-int64_t sumsq_max_partials() { return RED_BLOCKS; }
+int64_t sumsq_max_partials() { return RED_MAX_BLOCKS; }
+
+int num_sms() {
+  constexpr int MAXDEV = 64;
+  static std::atomic<int> cached[MAXDEV];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) return 152;
+  const int c = cached[dev].load(std::memory_order_relaxed);
+  if (c > 0) return c;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    return 152;
+  }
+  cached[dev].store(n, std::memory_order_relaxed);   // concurrent first calls store the same value
+  return n;
+}
 
 cudaError_t launch_hosvd_report(const HosvdReportArgs &a, cudaStream_t st) {
   count_launch(1);
@@ -139,9 +163,10 @@ cudaError_t launch_hosvd_report(const HosvdReportArgs &a, cudaStream_t st) {
 
 cudaError_t launch_sumsq(const float *x, int64_t n, double *partials, int *n_partials,
                          cudaStream_t st) {
-  *n_partials = RED_BLOCKS;
+  const int blocks = red_blocks();
+  *n_partials = blocks;
   count_launch(1);
-  sumsq_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, n, partials);
+  sumsq_kernel<<<blocks, RED_THREADS, 0, st>>>(x, n, partials);
   return cudaGetLastError();
 }
 
@@ -162,7 +187,7 @@ cudaError_t launch_check_q(const float *Q, int64_t n, int64_t p, float tol, int3
 
 cudaError_t launch_check_finite(const float *x, int64_t n, int32_t *status, cudaStream_t st) {
   count_launch(1);
-  check_finite_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(x, n, status);
+  check_finite_kernel<<<red_blocks(), RED_THREADS, 0, st>>>(x, n, status);
   return cudaGetLastError();
 }
 

@@ -216,7 +216,7 @@ cudaError_t launch_select(const SelectArgs &a, cudaStream_t st) {
   // at most one CTA per SM: each CTA stages all of sigma once, its 32 warps
   // then take entries in turn
   int blocks = (int)((N + 31) / 32);
-  if (blocks > 152) blocks = 152;
+  if (blocks > num_sms()) blocks = num_sms();
   cudaError_t e;
   if (use_smem) {
     e = cudaFuncSetAttribute(select_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -440,6 +440,56 @@ def test_hosvd_full_rank_is_projection():
     np.testing.assert_allclose(Ak, oracle.mode3(oracle.mode3(A, Q.T), Q), atol=1e-12)
 
 
+def _orth(n, seed):
+    q, r = np.linalg.qr(np.random.default_rng(seed).standard_normal((n, n)))
+    return q * np.sign(np.diag(r))
+
+
+def test_hosvd_truncation_exact_on_a_diagonal_tucker_core():
+    """Sec. 4.2 truncated HOSVD on A = G x1 U1 x2 U2 x3 U3 with a superdiagonal
+    core G(r,r,r) = g_r, g strictly decreasing, and random orthogonal U_i (none
+    symmetric): the mode-1 and mode-2 Grams are U_i diag(g^2) U_i^T, so the
+    leading k_i eigenvectors are the first k_i columns of U_i, and with Q = U3
+    (first p columns) the HOSVD(k1, k2, p) approximation is exactly
+    sum_{r < min(k1, k2, p)} g_r u1_r o u2_r o u3_r with squared error
+    sum_{r >= min(k1, k2, p)} g_r^2.  Trailing eigenvectors, or eigenvector
+    matrices read by rows instead of columns, give other tensors and errors."""
+    n1, n2, n3, p = 7, 6, 8, 4
+    g = np.array([10.0, 7.0, 5.0, 3.0, 2.0, 1.5])
+    U1, U2, U3 = _orth(n1, 31), _orth(n2, 32), _orth(n3, 33)
+    R = len(g)
+    A = np.einsum("r,ir,jr,tr->tij", g, U1[:, :R], U2[:, :R], U3[:, :R])
+    Q = U3[:, :p]
+    for k1, k2 in [(1, 6), (2, 3), (3, 2), (4, 4), (5, 6), (7, 6)]:
+        kk = min(k1, k2, p)
+        ref = np.einsum("r,ir,jr,tr->tij", g[:kk], U1[:, :kk], U2[:, :kk], U3[:, :kk])
+        Ak, err2 = oracle.hosvd(A, k1, k2, Q)
+        np.testing.assert_allclose(Ak, ref, atol=1e-11)
+        assert err2 == pytest.approx(float(np.sum(g[kk:] ** 2)), rel=1e-10, abs=1e-10)
+
+
+def test_hosvd_matches_svd_of_the_unfoldings():
+    """Sec. 4.2 truncated HOSVD against the same construction from LAPACK's SVD
+    of the mode-1 and mode-2 unfoldings (leading k_i left singular vectors):
+    A_k = A x1 U1 U1^T x2 U2 U2^T x3 Q Q^T, |A - A_k|^2 = |A|^2 - |core|^2 with
+    core = A x1 U1^T x2 U2^T x3 Q^T (orthogonal projections).  Random data has
+    distinct singular values, so the truncated subspaces and A_k are unique."""
+    n1, n2, n3, p = 9, 7, 10, 5
+    A = RNG.standard_normal((n3, n1, n2))
+    Q = _orth(n3, 41)[:, :p]
+    A1 = A.transpose(1, 0, 2).reshape(n1, -1)       # mode-1 unfolding (i, (t, j))
+    A2 = A.transpose(2, 0, 1).reshape(n2, -1)       # mode-2 unfolding (j, (t, i))
+    W1 = np.linalg.svd(A1)[0]
+    W2 = np.linalg.svd(A2)[0]
+    for k1, k2 in [(3, 2), (2, 5), (6, 6), (9, 7)]:
+        V1, V2 = W1[:, :k1], W2[:, :k2]
+        core = np.einsum("tij,ia,jb,tc->cab", A, V1, V2, Q)
+        ref = np.einsum("cab,ia,jb,tc->tij", core, V1, V2, Q)
+        Ak, err2 = oracle.hosvd(A, k1, k2, Q)
+        np.testing.assert_allclose(Ak, ref, atol=1e-11)
+        assert err2 == pytest.approx(float(np.sum(A ** 2) - np.sum(core ** 2)), rel=1e-9)
+
+
 def test_metrics_storage_formulas():
     """Sec. 5.1.2 storage counts and CR."""
     assert oracle.storage_tsvdq(120, 160, 5, 50) == 120 * 5 * 50 + 5 * 160 * 50

@@ -5,9 +5,12 @@ workspace argument and runs on the library's fixed device scratch array.
 
 Checked through the C ABI against the existing tsvdqII (which takes a
 caller-allocated workspace), on two calls in a row with different shapes, with
-the tolerances of the parity tests; then a shape whose workspace exceeds the
-fixed scratch must be rejected before anything runs.  This file is collected
-last so that a failure here cannot hide the results of the other GPU tests.
+the tolerances of the parity tests; a third call, made directly through the C
+ABI into buffers allocated beforehand, must leave the device's free memory
+unchanged and reproduce the earlier result; a shape whose workspace exceeds
+the fixed scratch must be rejected before anything runs.  This file is
+collected last so that a failure here cannot hide the results of the other
+GPU tests.
 """
 import ctypes
 
@@ -43,7 +46,6 @@ def _compare(b, A, Q, gamma):
     nA = _norm(Ad)
     assert _norm(got.Ak - ref.Ak) <= 1e-6 * nA
     kappa = int(r_ref.kappa)
-    l, m = A.shape[1], A.shape[2]
     s_ref, s_got = ref.s[:kappa].double(), got.s[:kappa].double()
     assert float((s_got - s_ref).norm()) <= 1e-5 * float(s_ref.norm())
     for (Ur, sr, Vr), (Ug, sg, Vg) in zip(ref.slices(), got.slices()):
@@ -52,20 +54,45 @@ def _compare(b, A, Q, gamma):
             dg = (Ug.double() * sg.double()) @ Vg.double().T
             assert float((dg - dr).norm()) <= 1e-6 * nA
     assert abs(r_got.err2 - r_ref.err2) <= 1e-6 * r_ref.normA2
-    return got
+    return Ad, Qd, got
 
 
 def test_noalloc_matches_tsvdqII_two_calls_in_a_row():
     b = _b()
     A1, _ = inputs.tiny()
-    _compare(b, A1, inputs.dct_q(16, 4), 0.8)                       # first call: set-up
+    Q1 = inputs.dct_q(16, 4)
+    Ad, Qd, first = _compare(b, A1, Q1, 0.8)                        # first call: set-up
     A2 = inputs.gaussian((45, 37, 53), seed=21)
     _compare(b, A2, inputs.random_q(45, 7, seed=22), 0.9)           # second call, other shape
-    # a third call allocates nothing on the device
+    # a third call, straight through the C ABI into buffers allocated before
+    # the first free-memory reading: nothing is allocated or freed in between
+    n, l, m = A1.shape
+    p, r = Q1.shape[1], min(l, m)
+    dev = Ad.device
+    rho = torch.empty(p, dtype=torch.int32, device=dev)
+    offs = torch.empty(p + 1, dtype=torch.int64, device=dev)
+    Uh = torch.empty(p * r * l, dtype=torch.float32, device=dev)
+    s = torch.empty(p * r, dtype=torch.float32, device=dev)
+    Vh = torch.empty(p * r * m, dtype=torch.float32, device=dev)
+    Ak = torch.empty((n, l, m), dtype=torch.float32, device=dev)
+    rep = torch.zeros(b.REPORT_BYTES, dtype=torch.uint8, device=dev)
+    opts = b.pp_opts()
+    P = lambda t: ctypes.c_void_p(t.data_ptr())
+    torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
-    _compare(b, A1, inputs.dct_q(16, 4), 0.8)
+    st = b.lib().tsvdqII_noalloc(P(Ad), P(Qd), l, m, n, p, 0.8, P(rho), P(offs), P(Uh), P(s),
+                                 P(Vh), P(Ak), P(rep), ctypes.byref(opts),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
+    assert st == 0, b.status_str(st)
     assert free0 == free1
+    assert b.read_report(rep).status == 0
+    # the same inputs give the same result as the first call
+    assert torch.equal(rho, first.rho) and torch.equal(offs, first.offs)
+    kappa = int(offs[-1])
+    assert torch.equal(s[:kappa], first.s[:kappa])
+    assert torch.equal(Ak, first.Ak)
 
 
 def test_noalloc_video_workload_fits():
@@ -78,7 +105,19 @@ def test_noalloc_rejects_shapes_beyond_the_scratch():
     b = _b()
     need = b.workspace_bytes(b.PP_OP_TSVDQII, l=120, m=160, n=300, p=300)
     assert need > 16 * 1024 * 1024
-    fake = ctypes.c_void_p(1 << 20)          # never dereferenced: rejected on the host
-    st = b.lib().tsvdqII_noalloc(fake, fake, 120, 160, 300, 300, 0.99, fake, fake, fake, fake,
-                                 fake, None, None, None, None)
+    # Null pointers throughout: the oversize check must reject the call on the
+    # host; if the check order ever regressed, the null check of tsvdqII would
+    # answer PP_EINVAL and still nothing would be enqueued.
+    st = b.lib().tsvdqII_noalloc(None, None, 120, 160, 300, 300, 0.99, None, None, None, None,
+                                 None, None, None, None, None)
+    assert st == b.PP_EINVAL
+    # With every pointer a (small) valid device buffer the size limit is what
+    # rejects it.  Nothing can be enqueued here even if that check regressed:
+    # tsvdqII itself refuses a workspace smaller than the shape needs, and the
+    # assertion above shows the 16 MiB scratch is smaller.
+    dev = torch.device("cuda")
+    buf = torch.empty(256, dtype=torch.float32, device=dev)
+    P = ctypes.c_void_p(buf.data_ptr())
+    st = b.lib().tsvdqII_noalloc(P, P, 120, 160, 300, 300, 0.99, P, P, P, P, P, None, None, None,
+                                 None)
     assert st == b.PP_EWORKSPACE
