@@ -42,87 +42,18 @@
 #include <mutex>
 
 #include "pp_internal.h"
+#include "pp_tc.cuh"
 
 namespace pp {
 namespace {
 
+using namespace tc;
+
 constexpr int TM = 128;        // pixels per CTA (MMA M)
 constexpr int TK = 32;         // S per stage: one 128-byte swizzle row of tf32
 constexpr int THREADS = 256;   // two threads per pixel row (halves of K and of the columns)
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz
 constexpr int TMA_STAGES = 4;                     // raw FP32 chunks in flight (TMA path)
 constexpr int RAW_BYTES = TK * TM * 4;            // one 32 x 128 FP32 box
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// x rounded to the nearest tf32 value (10 stored mantissa bits), ties away
-// from zero, in the FP32 container: half a tf32 ulp is added to the magnitude
-// bits and the 13 bits tf32 drops are cleared (a carry into the exponent is the
-// correct rounding up).  Integer ALU work, unlike the conversion pipe; the same
-// value as the PTX cvt.rna.tf32.f32 for every finite x.
-__device__ __forceinline__ float tf32_rna(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
-
-// byte offset of element (row, k), k < 32, in a K-major SW128 tile
-__device__ __forceinline__ uint32_t sw128_chunk(int row, int chunk) {
-  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + (((chunk ^ row) & 7) << 4));
-}
-
-// tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row
-// atoms 1024 bytes apart (stride byte offset), version field 1.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-  return d;
-}
-
-// instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M x N
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
-  return (1u << 4)                      // D format f32
-         | (2u << 7)                    // A format tf32
-         | (2u << 10)                   // B format tf32
-         | ((uint32_t)(N >> 3) << 17)   // N / 8
-         | ((uint32_t)(M >> 4) << 24);  // M / 16
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
-               : "memory");
-}
 
 // one 2-D box of the tensor map at (x = pixel, y = S row) into shared memory,
 // completing `bytes` on the mbarrier
@@ -135,16 +66,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-// bounded wait: false after ~WAIT_CYCLES
-__device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try(mbar, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
 constexpr int NT = 64;   // output slices per CTA (MMA N)
+
+// Batch and layout of a product launch: member z reads M at Qm + z sMz and X at
+// X + z sXz, X(s, n) = X[s sxc + n sxn], and writes Y + z sYz; s_total > 0
+// marks a split of one contraction of s_total terms into members of S terms.
+struct BatchStrides {
+  int64_t sMz = 0, sXz = 0, sYz = 0;
+  int64_t sxc = 0, sxn = 1;
+  int64_t s_total = 0;
+};
 
 // warp w adds columns [32 (w / 4), 32 (w / 4) + 32) of TMEM lanes 32 (w % 4) ... + 31 of
 // buffer `buf` (chunk partial sums) into acc[] (one TMEM lane per thread)
@@ -173,7 +104,8 @@ template <bool TMA>
 __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
     const __grid_constant__ CUtensorMap tmap, const float *__restrict__ Qm, int64_t sr,
     int64_t sc, const float *__restrict__ X,
-    float *__restrict__ Y, int64_t P, int64_t S, int64_t N, const float *__restrict__ Aref,
+    float *__restrict__ Y, int64_t P, int64_t S, int64_t N, const BatchStrides bz,
+    const float *__restrict__ Aref,
     double *__restrict__ errp, double *__restrict__ xpart, double *__restrict__ ypart,
     int32_t *status) {
   // stage layout (bytes): A_hi 16K | A_lo 16K | B_hi 8K | B_lo 8K
@@ -189,6 +121,19 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   __shared__ double red[THREADS / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // batch member z (blockIdx.z): its operands and output; split-K members
+  // (s_total > 0) each take S of the s_total contraction terms, the last fewer
+  {
+    const int64_t z = blockIdx.z;
+    Qm += z * bz.sMz;
+    X += z * bz.sXz;
+    if (Y) Y += z * bz.sYz;
+    if (bz.s_total > 0) {
+      const int64_t rem = bz.s_total - z * S;
+      S = rem < S ? rem : S;
+    }
+  }
+  const int64_t sxc = bz.sxc, sxn = bz.sxn;
   const int64_t n0 = (int64_t)blockIdx.x * TM;
   const int64_t y0 = (int64_t)blockIdx.y * NT;
   const bool do_x = xpart != nullptr && blockIdx.y == 0;
@@ -247,7 +192,7 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
 #pragma unroll
     for (int k = 0; k < TK / 2; ++k) {
       const int64_t s = s0 + khalf * (TK / 2) + k;
-      if (!TMA) va[k] = (pix < N && s < S) ? X[s * N + pix] : 0.f;
+      if (!TMA) va[k] = (pix < N && s < S) ? X[s * sxc + pix * sxn] : 0.f;
       vb[k] = (row < NT && trow < P && s < S) ? Qm[trow * sr + s * sc] : 0.f;
     }
   };
@@ -473,9 +418,38 @@ cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), 1);
+  BatchStrides bz;
+  bz.sxc = N;
   count_launch(1);
-  kern<<<grid, THREADS, smem, st>>>(map, Qm, sr, sc, X, Y, P, S, N, Aref, errp, xpart, ypart,
-                                    status);
+  kern<<<grid, THREADS, smem, st>>>(map, Qm, sr, sc, X, Y, P, S, N, bz, Aref, errp, xpart,
+                                    ypart, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_tc(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                              const float *X, int64_t sXz, int64_t sxc, int64_t sxn, float *Y,
+                              int64_t sYz, int64_t P, int64_t S, int64_t N, int64_t batch,
+                              int64_t s_total, int32_t *status, cudaStream_t st) {
+  if (batch < 1 || P < 1 || N < 1) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const size_t smem = tc_smem(false);
+  cudaError_t e = cudaFuncSetAttribute(mode3_tc_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BatchStrides bz;
+  bz.sMz = sMz;
+  bz.sXz = sXz;
+  bz.sYz = sYz;
+  bz.sxc = sxc;
+  bz.sxn = sxn;
+  bz.s_total = s_total;
+  const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), (unsigned)batch);
+  count_launch(1);
+  mode3_tc_kernel<false><<<grid, THREADS, smem, st>>>(map, Mm, sr, sc, X, Y, P, S, N, bz,
+                                                      nullptr, nullptr, nullptr, nullptr,
+                                                      status);
   return cudaGetLastError();
 }
 

@@ -27,21 +27,12 @@ __device__ inline void set_status(int32_t *status, int32_t code) {
 }
 
 // ---------------------------------------------------------------- GEMMs
-// Y (P x N, row-major, ldY = N) = M (P x S) * X (S x N, row-major), with
-// M(r, c) = Qm[r * sr + c * sc].  When Aref != nullptr the launch also writes
-// sum (Aref - Y)^2 over each CTA tile to err_partials[CTA] (FP64); Y may then
-// be nullptr (error only).  Optional energy partials: xpart gets *n_xpart sums
-// of X^2 (each X entry counted once), ypart one sum of Y^2 per CTA
-// (*n_partials of them).
-cudaError_t launch_mode3_gemm(const float *Qm, int64_t sr, int64_t sc, const float *X,
-                              float *Y, int64_t P, int64_t S, int64_t N, const float *Aref,
-                              double *err_partials, int *n_partials, cudaStream_t st,
-                              double *xpart = nullptr, int *n_xpart = nullptr,
-                              double *ypart = nullptr);
-int64_t mode3_gemm_max_partials(int64_t P, int64_t N);
-
-// Tensor-core (tcgen05, 3-pass split TF32) version of launch_mode3_gemm with
-// the same operands and fused sums; partial counts from mode3_tc_partials.
+// Y (P x N, row-major, ldY = N) = M (P x S) * X (S x N, row-major) on the
+// tensor cores (tcgen05, 3-pass split TF32), M(r, c) = Qm[r * sr + c * sc].
+// When Aref != nullptr the launch also writes sum (Aref - Y)^2 over each CTA
+// tile to errp[CTA] (FP64); Y may then be nullptr (error only).  Optional
+// energy partials: xpart gets *n_xpart sums of X^2 (each X entry counted
+// once), ypart one sum of Y^2 per CTA; partial counts from mode3_tc_partials.
 // A bounded wait that expires writes PP_ETIMEOUT to *status (if non-null).
 cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
@@ -49,7 +40,18 @@ cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float
                             int32_t *status, cudaStream_t st);
 int64_t mode3_tc_partials(int64_t P, int64_t N);
 
-// Batched FP32 GEMM Y[z] (P x N) = M[z] (P x S) * X[z] (S x N), M(r, c) =
+// The same tensor-core product over a batch (grid z): member z computes
+// Y[z] (P x N, row-major) = M[z] (P x S) X[z] (S x N) with M(r, c) =
+// Mm[z sMz + r sr + c sc] and X(c, n) = X[z sXz + c sxc + n sxn], Y at
+// Y + z sYz.  s_total > 0: the members are the K-chunks of one contraction of
+// s_total terms (member z holds terms z S .. min(s_total, (z + 1) S) - 1, its
+// operand offsets given by sMz and sXz).
+cudaError_t launch_batched_tc(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                              const float *X, int64_t sXz, int64_t sxc, int64_t sxn, float *Y,
+                              int64_t sYz, int64_t P, int64_t S, int64_t N, int64_t batch,
+                              int64_t s_total, int32_t *status, cudaStream_t st);
+
+// Batched product Y[z] (P x N) = M[z] (P x S) * X[z] (S x N) (launch_batched_tc), M(r, c) =
 // Mm[z*sMz + r*sr + c*sc], X and Y row-major with leading dimension N; a batch
 // stride of 0 broadcasts an operand over the batch.
 // X may be strided: X(c, n) = X[z*sXz + c*sxc + n*sxn] (sxc < 0: row-major, sxc = N).
