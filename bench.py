@@ -40,7 +40,7 @@ L, M, N, P, GAMMA = 120, 160, 300, 50, 0.99
 WORKLOAD = "video-shaped tSVDQII 120x160x300 (l x m x frames), Q = U3 leading p=50, gamma=0.99"
 METRIC = "tensor entries compressed/sec (tSVDQ)"
 UNIT = "entries/s"
-FP32_LANES_PER_SM, SMS = 128, 152
+FP32_LANES_PER_SM = 128
 
 
 def nominal_svd_flops(l, m, p):
@@ -48,6 +48,44 @@ def nominal_svd_flops(l, m, p):
     (a >= b): 4ab^2 + 8b^3, times p slices."""
     a, b = max(l, m), min(l, m)
     return p * (4.0 * a * b * b + 8.0 * b ** 3)
+
+
+def pipeline_roofline(l, m, n, p, kappa, hbm_gbs, fp32_tflops, stage_ms):
+    """T_roof = sum of the stage bounds of the hot path (algorithmic work per
+    tensor): projection 4(lmn + np + plm) bytes at HBM bandwidth; facewise SVD
+    the nominal 4ab^2 + 8b^3 flops per slice at the FP32 FMA peak; select 8 p b
+    bytes; rebuild + back-projection 4 lmn + 4 kappa (l + m) + 4 np bytes.
+    frac = T_roof / T_step (the measured stage sum)."""
+    b = min(l, m)
+    t = {"projection": 4.0 * (l * m * n + n * p + p * l * m) / (hbm_gbs * 1e9),
+         "svd": nominal_svd_flops(l, m, p) / (fp32_tflops * 1e12),
+         "select": 8.0 * p * b / (hbm_gbs * 1e9),
+         "rebuild_backproj": 4.0 * (l * m * n + kappa * (l + m) + n * p) / (hbm_gbs * 1e9)}
+    t_roof = sum(t.values())
+    t_step = sum(stage_ms) / 1e3
+    return {"t_roof_ms": 1e3 * t_roof, "t_step_ms": 1e3 * t_step, "frac": t_roof / t_step,
+            "stage_bound_ms": {k: 1e3 * v for k, v in t.items()}}
+
+
+def measure_peaks(torch, binding, stream):
+    """FP32 FMA and tcgen05 tf32 throughput from the library's probe kernels
+    (CUDA events on the launching stream, best of 3 after a warm-up), at the
+    clocks the GPU runs at."""
+    out = {}
+    for kind, name, reps in ((0, "fp32_fma_tflops", 16384), (1, "tf32_tensor_tflops", 20000)):
+        best = None
+        with torch.cuda.stream(stream):
+            binding.peak_probe(kind, reps, stream)
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fl = binding.peak_probe(kind, reps, stream)
+                e1.record(stream)
+                e1.synchronize()
+                v = fl / (e0.elapsed_time(e1) / 1e3) / 1e12
+                best = v if best is None else max(best, v)
+        out[name] = best
+    return out
 
 
 def stage_traffic(kernels):
@@ -230,6 +268,180 @@ class Runner:
         return self.b.read_report(self.rep)
 
 
+class TruncRunner:
+    """Preallocated buffers and a direct C-ABI call for one tsvdq_trunc (Alg. 4.1)
+    configuration."""
+
+    def __init__(self, A_dev, Q_dev, k, torch, binding):
+        import ctypes
+        self.t, self.b, self.ct = torch, binding, ctypes
+        self.A, self.Q, self.k = A_dev, Q_dev, k
+        n, l, m = A_dev.shape
+        p = Q_dev.shape[1]
+        self.dims = (l, m, n, p)
+        d = A_dev.device
+        self.Uh = torch.empty(p * l * k, dtype=torch.float32, device=d)
+        self.s = torch.empty(p * k, dtype=torch.float32, device=d)
+        self.Vh = torch.empty(p * m * k, dtype=torch.float32, device=d)
+        self.Ak = torch.empty((n, l, m), dtype=torch.float32, device=d)
+        self.rep = torch.zeros(binding.REPORT_BYTES, dtype=torch.uint8, device=d)
+        nb = binding.workspace_bytes(binding.PP_OP_TSVDQ, l=l, m=m, n=n, p=p, k=k)
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=d)
+        self.opts = binding.pp_opts()
+
+    def __call__(self, stream):
+        P_ = lambda x: self.ct.c_void_p(x.data_ptr())
+        l, m, n, p = self.dims
+        st = self.b.lib().tsvdq_trunc(P_(self.A), P_(self.Q), l, m, n, p, int(self.k), P_(self.Uh),
+                                      P_(self.s), P_(self.Vh), P_(self.Ak), P_(self.rep),
+                                      self.ct.byref(self.opts), P_(self.ws), self.ws.numel(),
+                                      self.ct.c_void_p(stream.cuda_stream))
+        if st != 0:
+            raise RuntimeError(self.b.status_str(st))
+
+    def report(self):
+        return self.b.read_report(self.rep)
+
+
+def equal_error_gamma(binding, A_d, Qn_d, err_target):
+    """gamma' for the p = n (*M) path whose *Q-SVDII error is at most err_target:
+    the smallest K whose discarded energy plus projection error fits."""
+    n, l, m = A_d.shape
+    full = binding.tsvdq_trunc(A_d, Qn_d, min(l, m), want_ak=False)
+    import torch
+    torch.cuda.synchronize()
+    sig = full.s.double().cpu().numpy()
+    keys = np.sort((sig ** 2).ravel())[::-1]
+    c = np.cumsum(keys)
+    total = c[-1]
+    frep = full.report()
+    proj = max(frep.normA2 - frep.normAh2, 0.0)
+    need = total - (err_target - proj)
+    Kp = int(np.searchsorted(c, need, side="left")) + 1
+    Kp = min(max(Kp, 1), len(c))
+    return min(1.0, c[Kp - 1] / total)
+
+
+def sigma_error(sig_gpu, sig_ref, rel_floor=1e-3):
+    """Normwise |s~ - s|_2 / |s|_2 over all slices and the largest elementwise
+    relative error among the singular values >= rel_floor * max."""
+    sg, sr = np.asarray(sig_gpu, np.float64), np.asarray(sig_ref, np.float64)
+    nw = float(np.linalg.norm(sg - sr) / np.linalg.norm(sr))
+    big = sr >= rel_floor * sr.max()
+    ew = float(np.max(np.abs(sg[big] - sr[big]) / sr[big])) if big.any() else 0.0
+    return {"normwise": nw, "max_rel_retained": ew}
+
+
+def run_hyperspectral(args, torch, binding, stream, dev, hbm, fp32_peak):
+    """The hyperspectral-shaped workload (512 x 512 x 224, Q = U3 with p in {10,
+    25, 50, 100}; tSVDQII at gamma 0.99 and 0.9, fixed rank k in {5, 20, 50}),
+    each timed with stage events (best of 2 after a warm-up; A is 235 MB, larger
+    than L2), its pipeline roofline fraction, and the p = n = 224 (*M) path at
+    equal reconstruction error for p = 10 and p = 100.  Singular values of
+    slice 0 at p = 10 are compared with the oracle's."""
+    from paper_2409_19402_gb300 import inputs
+    A = inputs.hyperspectral()
+    n, l, m = A.shape
+    A_d = torch.from_numpy(A).to(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for e in ev:
+        e.record(stream)
+    stream.synchronize()
+
+    def time_run(run):
+        binding.set_stage_events(ev)
+        best = None
+        with torch.cuda.stream(stream):
+            run(stream)
+            for _ in range(2):
+                run(stream)
+                stream.synchronize()
+                st = [ev[j].elapsed_time(ev[j + 1]) for j in range(5)]
+                if best is None or sum(st) < sum(best):
+                    best = st
+        binding.set_stage_events(None)
+        return best
+
+    out = {"workload": "hyperspectral-shaped 512x512x224, Q = U3 leading p", "configs": []}
+    for p in (10, 25, 50, 100):
+        Qn = inputs.u3_q(A, p)
+        Q_d = torch.from_numpy(Qn).to(dev)
+        for kind, par in (("tsvdqII", 0.99), ("tsvdqII", 0.9), ("tsvdq_trunc", 5),
+                          ("tsvdq_trunc", 20), ("tsvdq_trunc", 50)):
+            run = (Runner(A_d, Q_d, par, torch, binding) if kind == "tsvdqII"
+                   else TruncRunner(A_d, Q_d, par, torch, binding))
+            st = time_run(run)
+            rep = run.report()
+            kappa = int(rep.kappa)
+            ms = sum(st)
+            pipe = pipeline_roofline(l, m, n, p, kappa, hbm, fp32_peak, st)
+            svd_tf = nominal_svd_flops(l, m, p) / (st[1] / 1e3) / 1e12
+            cfg = {"p": p, kind == "tsvdqII" and "gamma" or "k": par, "op": kind,
+                   "ms_per_step": ms, "value": l * m * n / (ms / 1e3), "unit": UNIT,
+                   "stages_ms": dict(zip(("projection", "svd", "select", "factors_rebuild",
+                                          "backproj_errors"), st)),
+                   "svd_frac_fp32": svd_tf / fp32_peak, "pipeline_frac": pipe["frac"],
+                   "kappa": kappa, "sweeps": int(rep.sweeps), "status": int(rep.status),
+                   "RE": math.sqrt(rep.err2 / rep.normA2)}
+            if kind == "tsvdqII" and par == 0.99 and p in (10, 100):
+                # the full invertible *M form at equal reconstruction error
+                Qfull = torch.from_numpy(inputs.u3_q(A, n)).to(dev)
+                g2 = equal_error_gamma(binding, A_d, Qfull, rep.err2)
+                runn = Runner(A_d, Qfull, g2, torch, binding)
+                stn = time_run(runn)
+                repn = runn.report()
+                cfg["pn_compare"] = {"p": n, "gamma": g2, "ms_per_step": sum(stn),
+                                     "err2": repn.err2, "err2_target": rep.err2,
+                                     "kappa": int(repn.kappa),
+                                     "speedup_p_lt_n": sum(stn) / ms}
+                del runn, Qfull
+            out["configs"].append(cfg)
+            del run
+        if p == 10:   # every singular value of slice 0, for the oracle comparison
+            full = binding.tsvdq_trunc(A_d, Q_d, min(l, m), want_ak=False)
+            torch.cuda.synchronize()
+            out["_sig0_p10"] = full.s[0].double().cpu().numpy()
+            out["_inputs_p10"] = (A, Qn)
+            del full
+    return out
+
+
+def cpu_baseline_leg(args, A, Qp, sig_gpu_video, hs):
+    """The oracle on the host cores: the video workload's full tSVDQII, single
+    thread (the reported baseline) and OpenMP over slices (all cores), and one
+    hyperspectral slice's SVD (p = 10, slice 0).  The same oracle outputs give
+    the singular-value error of the GPU results (normwise over every slice of
+    the video workload; slice 0 of the hyperspectral one)."""
+    import oracle
+    t0 = time.perf_counter()
+    ref = oracle.tsvdqII(A, Qp, GAMMA)
+    dt = time.perf_counter() - t0
+    cpu = {"value": L * M * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
+           "seconds": dt}
+    sig_err = {"video": sigma_error(sig_gpu_video, ref.sig_all)}
+    cpu_omp = None
+    if oracle.has_openmp():
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        oracle.tsvdqII(A, Qp, GAMMA, omp=True)
+        dt2 = time.perf_counter() - t0
+        cpu_omp = {"value": L * M * N / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "one full oracle tsvdqII step, OpenMP over slices and mode-3 "
+                             "output slices (same arithmetic per slice), all host cores",
+                   "seconds": dt2}
+    if hs is not None and "_sig0_p10" in hs:
+        Ah_A, Qn = hs.pop("_inputs_p10")
+        t0 = time.perf_counter()
+        Ah0 = oracle.mode3(Ah_A, np.asarray(Qn, np.float64)[:, :1].T)[0]
+        s0 = oracle.svd(Ah0)[1]
+        dt3 = time.perf_counter() - t0
+        sig_err["hyperspectral_p10_slice0"] = sigma_error(hs.pop("_sig0_p10"), s0)
+        hs["cpu_baseline_sample"] = {"seconds": dt3, "cores": 1, "kind": "oracle",
+                                     "sample": "projection and SVD of slice 0 (512 x 512), p = 10"}
+    return cpu, cpu_omp, sig_err
+
+
 def timed_steps(run, steps, warmup, torch, flush, stream, stage_events=None):
     """Per-step CUDA-event times (ms) with an L2 flush before every step."""
     for _ in range(warmup):
@@ -347,7 +559,10 @@ def run_ours(args):
     # ---------------- dominant kernel roofline (Jacobi SVD, stage 1 -> 2)
     peaks, peak_kind = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probes = measure_peaks(torch, binding, stream)
+    fp32_peak = probes["fp32_fma_tflops"]
+    fp32_nominal = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12     # TFLOP/s
     stage_mean = [statistics.mean(s[j] for s in stage_ms) for j in range(5)]
     jac_ms = stage_mean[1]
     flops = nominal_svd_flops(L, M, P)
@@ -356,13 +571,18 @@ def run_ours(args):
     # vectors of up to 176 entries, else the shared-memory one
     qr_kernel = "qrcp_reg_kernel" if min(L, M) <= 128 and max(L, M) <= 176 else "qrcp_kernel"
     stage_kernels = ([qr_kernel] if tuned[3] else []) + ["jacobi_cluster_kernel"]
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    pipe = pipeline_roofline(L, M, N, P, int(rep.kappa), hbm, fp32_peak, stage_mean)
     roofline = {"kernel": " + ".join(stage_kernels) + " (facewise SVD stage)", "bound": "alu",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": stage_traffic(stage_kernels),
-                "peak_kind": f"FP32 FMA: {SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                             f"{sm_max:.0f} MHz ({peak_kind} sm_max_mhz)",
-                "work": "nominal 4ab^2+8b^3 per slice (Golub-Kahan-Reinsch), p=50"}
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
+                "peak_kind": "measured: FP32 FMA probe kernel (pp_peak_probe kind 0) on this "
+                             f"GPU; nominal {sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                             f"{sm_max:.0f} MHz = {fp32_nominal:.1f}",
+                "work": "nominal 4ab^2+8b^3 per slice (Golub-Kahan-Reinsch), p=50",
+                "pipeline_frac": pipe["frac"], "pipeline": pipe,
+                "hbm_peak_gbs": hbm, "hbm_peak_kind": f"{peak_kind} (MEASURED_PEAKS.json copy)",
+                "probes": probes}
     proj_bytes = 4.0 * (L * M * N + N * P + P * L * M)
     back_bytes = 4.0 * (L * M * N * 2 + P * L * M + N * P)  # read A_k-hat and A, write A_k
     stages = {"projection_ms": stage_mean[0], "jacobi_ms": stage_mean[1],
@@ -416,18 +636,23 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world)
 
+    # ---------------- hyperspectral-shaped workload (N = 1)
+    hs = None
+    if world == 1 and not args.no_hyperspectral:
+        hs = run_hyperspectral(args, torch, binding, stream, dev, hbm, fp32_peak)
+
     # ---------------- oracle CPU baseline (rank 0, N = 1 only)
-    cpu = None
+    cpu = cpu_omp = sig_err = None
     if world == 1 and not args.no_cpu:
-        import oracle
-        t0 = time.perf_counter()
-        oracle.tsvdqII(A, Qp, GAMMA)
-        dt = time.perf_counter() - t0
-        cpu = {"value": L * M * N / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "one full oracle tsvdqII step of the workload (FP64, single thread)",
-               "seconds": dt}
+        full = binding.tsvdq_trunc(A_d, Qp_d, min(L, M), want_ak=False)
+        torch.cuda.synchronize()
+        cpu, cpu_omp, sig_err = cpu_baseline_leg(args, A, Qp, full.s.double().cpu().numpy(), hs)
+    if hs is not None:
+        hs.pop("_sig0_p10", None)
+        hs.pop("_inputs_p10", None)
     return finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-                  per_step_launches, clk, t_wall, dist, tuned, batched, diff, cplx)
+                  per_step_launches, clk, t_wall, dist, tuned, batched, diff, cplx,
+                  hs=hs, cpu_omp=cpu_omp, sig_err=sig_err)
 
 
 def run_complex(args, torch, binding, A_d, stream, dev):
@@ -639,7 +864,8 @@ def run_e2e(args, torch, binding, run, A, Qp, stream, dist, dev, world):
 
 
 def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e, cpu,
-           per_step_launches, clk, t_wall, dist, tuned=None, batched=None, diff=None, cplx=None):
+           per_step_launches, clk, t_wall, dist, tuned=None, batched=None, diff=None, cplx=None,
+           hs=None, cpu_omp=None, sig_err=None):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -658,8 +884,11 @@ def finish(args, rank, world, rep, value, ms_per_step, roofline, stages, pn, e2e
             "batched_64": batched,
             "diff_step": diff,
             "complex_dft": cplx,
+            "hyperspectral": hs,
+            "sigma_error_vs_oracle": sig_err,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_baseline_openmp": cpu_omp,
             "gpu_launches": int(round(per_step_launches * args.steps)),
             "clocks": clk,
             "wall_s_timed_region": t_wall,
@@ -684,6 +913,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end host-buffer run")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-tensor batched run")
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation step run")
+    ap.add_argument("--no-hyperspectral", action="store_true",
+                    help="skip the hyperspectral-shaped runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

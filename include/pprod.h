@@ -17,11 +17,13 @@
  * Q.  The transformation is a real n x p matrix with orthonormal columns
  * (Q in St_{n,p}, Sec. 3), row-major FP32 (Q[s*p + t]).  With p = n and Q
  * square orthogonal every call computes the invertible *M form (Def. 2.4,
- * M = Q^T).  Complex Q is not supported.
+ * M = Q^T).  Complex Q (Q^H Q = I, e.g. rows of the DFT) with real data is
+ * taken by the separate *_c entry points below.
  *
  * Pointers.  Every array argument is a DEVICE pointer, unless stated
  * otherwise, owned by the caller: the library never allocates or frees
- * device memory.  Inputs are read only.  Outputs must not alias inputs.
+ * device memory (its one fixed device array, PP_NOALLOC_SCRATCH_BYTES, is
+ * part of its loaded module).  Inputs are read only.  Outputs must not alias inputs.
  * Calls needing scratch take a caller-allocated device workspace of at least
  * pp_workspace_bytes(op, shape) bytes, 256-byte aligned.
  *
@@ -392,6 +394,20 @@ PP_API pp_status tsvdqII_noalloc(const float *A, const float *Q, int64_t l, int6
  */
 PP_API void pp_set_stage_events(void *const *events, int32_t n);
 PP_API uint64_t pp_kernel_launches(void);
+
+/*
+ * pp_peak_probe: measure an arithmetic peak (instrumentation, no counterpart
+ * in the paper).  kind 0: FP32 FMA throughput (a full-device grid of
+ * independent register FMA chains, `reps` rounds); kind 1: tcgen05 kind::tf32
+ * tensor throughput (one CTA per SM issuing `reps` M128 N256 K8 MMAs from
+ * shared memory into TMEM).  Asynchronous on `stream`; the caller times it
+ * with CUDA events.  *flops (host) receives the floating-point operations the
+ * launch performs; a bounded wait that expires writes PP_ETIMEOUT to *status
+ * (device pointer, may be NULL).  PP_EINVAL for another kind, reps < 1 or a
+ * NULL flops.
+ */
+PP_API pp_status pp_peak_probe(int32_t kind, int64_t reps, double *flops, int32_t *status,
+                               void *stream);
 
 /*
  * Launch-shape tuning of the facewise Jacobi SVD (no counterpart in the paper).

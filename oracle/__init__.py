@@ -40,28 +40,44 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pp_oracle.c")
 _LIB = os.path.join(_HERE, "_pp_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "_pp_oracle_omp.so")   # same source, -fopenmp
 
 OR_OK, OR_EINVAL, OR_ENOCONV, OR_ENOMEM = 0, 1, 5, 9
 
 
 def build(force: bool = False) -> str:
-    """Compile pp_oracle.c with gcc into oracle/_pp_oracle.so (no GPU needed)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+    """Compile pp_oracle.c with gcc into oracle/_pp_oracle.so (no GPU needed), and
+    the same source with -fopenmp into oracle/_pp_oracle_omp.so (the multi-core
+    timing baseline; skipped where the compiler has no OpenMP)."""
+    for lib, extra in ((_LIB, []), (_LIB_OMP, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+            tmp = lib + f".tmp{os.getpid()}"
+            r = subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp,
+                                _SRC, "-lm"], capture_output=True, text=True)
+            if r.returncode != 0:
+                if extra:          # no OpenMP: the single-thread library still serves
+                    continue
+                raise RuntimeError(f"gcc failed building the oracle:\n{r.stderr}")
+            os.replace(tmp, lib)
     return _LIB
 
 
-_lib = None
+def has_openmp() -> bool:
+    """The OpenMP build of the oracle exists (after build())."""
+    build()
+    return os.path.exists(_LIB_OMP)
 
 
-def _L():
-    global _lib
-    if _lib is None:
+_libs = {}
+
+
+def _L(omp: bool = False):
+    key = bool(omp)
+    if key not in _libs:
         build()
-        lib = ctypes.CDLL(_LIB)
+        if key and not os.path.exists(_LIB_OMP):
+            raise OracleError("the OpenMP build of the oracle is not available")
+        lib = ctypes.CDLL(_LIB_OMP if key else _LIB)
         i64, dp = ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
         ip32, ip64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
         lib.or_mode3.argtypes = [dp, i64, i64, i64, dp, i64, dp]
@@ -85,8 +101,8 @@ def _L():
         for f in ("or_qprod", "or_mprod", "or_svd_jacobi", "or_tsvdq", "or_select_energy",
                   "or_tsvdqII", "or_sym_eig_jacobi", "or_hosvd", "or_householder_q"):
             getattr(lib, f).restype = ctypes.c_int
-        _lib = lib
-    return _lib
+        _libs[key] = lib
+    return _libs[key]
 
 
 def _f64(x) -> np.ndarray:
@@ -235,8 +251,10 @@ class TsvdqIIResult:
     report: Report
 
 
-def tsvdqII(A, Q, gamma: float, max_sweeps: int = 60) -> TsvdqIIResult:
-    """Alg. 4.2 (*Q-SVDII) with energy parameter gamma in (0, 1]."""
+def tsvdqII(A, Q, gamma: float, max_sweeps: int = 60, omp: bool = False) -> TsvdqIIResult:
+    """Alg. 4.2 (*Q-SVDII) with energy parameter gamma in (0, 1].  omp=True runs
+    the OpenMP build (slices and mode-3 output slices shared out over threads,
+    OMP_NUM_THREADS; the same arithmetic per slice)."""
     A, Q = _f64(A), _f64(Q)
     n, l, m = A.shape
     p = Q.shape[1]
@@ -246,7 +264,7 @@ def tsvdqII(A, Q, gamma: float, max_sweeps: int = 60) -> TsvdqIIResult:
     Uhp, sp, Vhp = np.empty(p * r * l), np.empty(p * r), np.empty(p * r * m)
     Ak, sig = np.empty((n, l, m)), np.empty((p, r))
     rep = _Report()
-    _check(_L().or_tsvdqII(_p(A), _p(Q), l, m, n, p, float(gamma), max_sweeps,
+    _check(_L(omp).or_tsvdqII(_p(A), _p(Q), l, m, n, p, float(gamma), max_sweeps,
                            rho.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                            offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                            _p(Uhp), _p(sp), _p(Vhp), _p(Ak), _p(sig), ctypes.byref(rep)),

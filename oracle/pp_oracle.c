@@ -55,6 +55,10 @@ typedef int64_t i64;
 void or_mode3(const double *X, i64 n1, i64 n2, i64 n3,
               const double *M, i64 q, double *Y)
 {
+    /* output slices are independent: with OpenMP (the multi-core baseline
+       build only) they are shared out over threads; the arithmetic of each
+       entry is the same loop in the same order either way */
+#pragma omp parallel for schedule(static)
     for (i64 t = 0; t < q; ++t)
         for (i64 i = 0; i < n1; ++i)
             for (i64 j = 0; j < n2; ++j) {
@@ -462,13 +466,21 @@ int or_tsvdqII(const double *A, const double *Q, i64 l, i64 m, i64 n, i64 p,
     }
     transpose(Q, n, p, Qt);
     or_mode3(A, l, m, n, Qt, p, Ah);                      /* step 2 */
-    int st = OR_OK;
-    for (i64 t = 0; t < p && st == OR_OK; ++t) {          /* step 3 */
+    int st = OR_OK, msw = 0;
+    /* step 3: the slices' SVDs are independent (shared out over threads in
+       the OpenMP build; each slice's arithmetic is unchanged) */
+#pragma omp parallel for schedule(dynamic) reduction(max : msw)
+    for (i64 t = 0; t < p; ++t) {
         int sw = 0;
-        st = or_svd_jacobi(Ah + t * l * m, l, m, Uf + t * l * r, sf + t * r,
-                           Vf + t * m * r, max_sweeps, &sw);
-        if (sw > rep->max_sweeps) rep->max_sweeps = sw;
+        const int e = or_svd_jacobi(Ah + t * l * m, l, m, Uf + t * l * r, sf + t * r,
+                                    Vf + t * m * r, max_sweeps, &sw);
+        if (sw > msw) msw = sw;
+        if (e != OR_OK) {
+#pragma omp critical
+            st = e;
+        }
     }
+    rep->max_sweeps = msw;
     if (st == OR_OK) {
         i64 K = 0;
         double kept = 0.0, total = 0.0;

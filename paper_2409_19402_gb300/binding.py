@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
         L.pp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         L.pp_set_stage_events.restype = None
         L.pp_kernel_launches.restype = ctypes.c_uint64
+        L.pp_peak_probe.argtypes = [i32, i64, ctypes.POINTER(ctypes.c_double), vp, vp]
+        L.pp_peak_probe.restype = i32
         _lib = L
     return _lib
 
@@ -139,6 +141,15 @@ def version() -> str:
 def kernel_launches() -> int:
     """Process-wide count of kernels launched by libpprod.so."""
     return int(lib().pp_kernel_launches())
+
+
+def peak_probe(kind: int, reps: int, stream=None) -> float:
+    """Enqueue the arithmetic-peak probe (0: FP32 FMA, 1: tcgen05 tf32) on
+    `stream`; returns the flops the launch performs (time it with events)."""
+    fl = ctypes.c_double(0.0)
+    _raise(lib().pp_peak_probe(int(kind), int(reps), ctypes.byref(fl), None, _stream(stream)),
+           "pp_peak_probe")
+    return fl.value
 
 
 def set_stage_events(events) -> None:

@@ -186,14 +186,14 @@ def _margin(sig_ref, gamma, K):
     return min(c[K - 1] - gamma * cN, gamma * cN - lo) / cN, keys
 
 
-def _tsvdqII_case(A, Q, gamma, **opts):
+def _tsvdqII_case(A, Q, gamma, oracle_omp=False, **opts):
     b = _b()
     out = b.tsvdqII(dev(A), dev(Q), gamma, **opts)
     full = b.tsvdq_trunc(dev(A), dev(Q), min(A.shape[1], A.shape[2]), want_ak=False, **opts)
     torch.cuda.synchronize()
     rep = out.report()
     assert rep.status == 0, b.status_str(rep.status)
-    ref = oracle.tsvdqII(A, Q, gamma)
+    ref = oracle.tsvdqII(A, Q, gamma, omp=oracle_omp and oracle.has_openmp())
     sig_gpu = host(full.s)                                   # every singular value
     # (1) bit-exact selection on the GPU's own singular values
     K2, rho2, kept2, total2 = oracle.select_energy(sig_gpu, gamma)

@@ -580,3 +580,16 @@ def test_qprod_gradient_matches_central_differences():
     np.testing.assert_allclose(S + S.T, 0.0, atol=1e-10)
     M = Q.T @ dQE
     np.testing.assert_allclose(dQ, dQE - Q @ (0.5 * (M + M.T)), atol=1e-12)
+
+
+def test_openmp_oracle_build_is_bitwise_the_serial_one():
+    """The multi-core baseline build shares out independent slices only: its
+    Alg. 4.2 results are bit-identical to the single-thread build's."""
+    if not oracle.has_openmp():
+        pytest.skip("no OpenMP in this compiler")
+    A = RNG.standard_normal((14, 9, 11))
+    Q = _rand_q(14, 6)
+    a = oracle.tsvdqII(A, Q, 0.9)
+    b = oracle.tsvdqII(A, Q, 0.9, omp=True)
+    assert np.array_equal(a.rho, b.rho) and np.array_equal(a.sig_all, b.sig_all)
+    assert np.array_equal(a.Ak, b.Ak) and a.report == b.report
