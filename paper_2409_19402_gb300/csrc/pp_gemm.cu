@@ -12,13 +12,16 @@ namespace pp {
 namespace {
 
 // ---------------------------------------------------------------- A B^T, split over K
-// out (R x S) (+)= sum over z of part[z], in z order
-__global__ void sum_parts_kernel(const float *__restrict__ part, int64_t count, int64_t nz,
-                                 float *__restrict__ out, int accumulate) {
+// out (R x S) (+)= sum over z of part[z], in z order; the parts hold R x S
+// (transposed = 0) or S x R (transposed = 1) products
+__global__ void sum_parts_kernel(const float *__restrict__ part, int64_t R, int64_t S, int64_t nz,
+                                 float *__restrict__ out, int accumulate, int transposed) {
+  const int64_t count = R * S;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
        e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t src = transposed ? (e % S) * R + e / S : e;
     float s = accumulate ? out[e] : 0.f;
-    for (int64_t z = 0; z < nz; ++z) s += part[z * count + e];
+    for (int64_t z = 0; z < nz; ++z) s += part[z * count + src];
     out[e] = s;
   }
 }
@@ -38,10 +41,16 @@ __global__ void stiefel_kernel(const float *__restrict__ Q, const float *__restr
 
 }  // namespace
 
-// Splits of the contraction of A B^T: enough (R/64 x S/128)-tile members to
-// cover the SMs three times, each with at least 256 of the K terms.
+// The product behind A B^T: the tensor-core tile puts 128 rows of its output
+// on the MMA's M and 64 on its N, so when S (the columns of A B^T) is the
+// smaller side the product is formed transposed, B A^T (S x R), with R on M.
+bool nt_transposed(int64_t R, int64_t S) { return S < R; }
+
+// Splits of the contraction: enough (64 x 128)-tile members to cover the SMs
+// three times, each with at least 256 of the K terms.
 int64_t nt_splits(int64_t R, int64_t S, int64_t K) {
-  const int64_t tiles = ((R + 63) / 64) * ((S + 127) / 128);
+  const int64_t rows = nt_transposed(R, S) ? S : R, cols = nt_transposed(R, S) ? R : S;
+  const int64_t tiles = ((rows + 63) / 64) * ((cols + 127) / 128);
   int64_t z = ((int64_t)num_sms() * 3 + tiles - 1) / tiles;
   const int64_t zmax = (K + 255) / 256;   // at least 256 of K per split
   if (z > zmax) z = zmax;
@@ -54,16 +63,19 @@ cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int6
   int64_t kchunk = (K + nz - 1) / nz;
   kchunk = (kchunk + 31) / 32 * 32;            // whole 32-term chunks per split
   const int64_t nzu = (K + kchunk - 1) / kchunk;
-  // member z: part[z] (R x S) = A[:, zk..] B[:, zk..]^T;  M(r, c) = A[r K + c],
-  // X(c, n) = B[n K + c]
-  cudaError_t e = launch_batched_tc(A, K, 1, kchunk, B, kchunk, 1, K, part, R * S, R, kchunk, S,
-                                    nzu, K, nullptr, st);
+  const bool tr = nt_transposed(R, S);
+  // member z: part[z] = A[:, zk..] B[:, zk..]^T (R x S), or its transpose
+  // B[:, zk..] A[:, zk..]^T (S x R); M(r, c) = first[r K + c], X(c, n) = second[n K + c]
+  const float *first = tr ? B : A, *second = tr ? A : B;
+  const int64_t P = tr ? S : R, N = tr ? R : S;
+  cudaError_t e = launch_batched_tc(first, K, 1, kchunk, second, kchunk, 1, K, part, R * S, P,
+                                    kchunk, N, nzu, K, nullptr, st);
   if (e != cudaSuccess) return e;
   const int64_t count = R * S;
   int blocks = (int)((count + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   count_launch(1);
-  sum_parts_kernel<<<blocks, 256, 0, st>>>(part, count, nzu, out, accumulate);
+  sum_parts_kernel<<<blocks, 256, 0, st>>>(part, R, S, nzu, out, accumulate, tr ? 1 : 0);
   return cudaGetLastError();
 }
 
