@@ -75,7 +75,16 @@ struct BatchStrides {
   int64_t sMz = 0, sXz = 0, sYz = 0;
   int64_t sxc = 0, sxn = 1;
   int64_t s_total = 0;
+  // contraction-contiguous operands with 16-byte aligned rows: a thread's 16
+  // consecutive terms come in as four 16-byte loads (register path)
+  int vec_x = 0, vec_m = 0;
 };
+
+// X(c, n) = X[c + n sxn] (sxc = 1) with every member's rows 16-byte aligned
+bool vec_rows(const float *base, int64_t stride, int64_t member_stride) {
+  return (reinterpret_cast<uintptr_t>(base) & 15) == 0 && stride % 4 == 0 &&
+         member_stride % 4 == 0;
+}
 
 // warp w adds columns [32 (w / 4), 32 (w / 4) + 32) of TMEM lanes 32 (w % 4) ... + 31 of
 // buffer `buf` (chunk partial sums) into acc[] (one TMEM lane per thread)
@@ -189,11 +198,36 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   float va[TK / 2], vb[TK / 2];
   auto load_chunk = [&](int c) {
     const int64_t s0 = (int64_t)c * TK;
+    const int64_t sk = s0 + khalf * (TK / 2);   // this thread's first term of the chunk
+    if (!TMA) {
+      if (bz.vec_x && pix < N && sk + TK / 2 <= S) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(X + pix * sxn + sk);
 #pragma unroll
-    for (int k = 0; k < TK / 2; ++k) {
-      const int64_t s = s0 + khalf * (TK / 2) + k;
-      if (!TMA) va[k] = (pix < N && s < S) ? X[s * sxc + pix * sxn] : 0.f;
-      vb[k] = (row < NT && trow < P && s < S) ? Qm[trow * sr + s * sc] : 0.f;
+        for (int q = 0; q < 4; ++q) {
+          const float4 t = p4[q];
+          va[4 * q] = t.x; va[4 * q + 1] = t.y; va[4 * q + 2] = t.z; va[4 * q + 3] = t.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < TK / 2; ++k) {
+          const int64_t s = sk + k;
+          va[k] = (pix < N && s < S) ? X[s * sxc + pix * sxn] : 0.f;
+        }
+      }
+    }
+    if (bz.vec_m && row < NT && trow < P && sk + TK / 2 <= S) {
+      const float4 *p4 = reinterpret_cast<const float4 *>(Qm + trow * sr + sk);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 t = p4[q];
+        vb[4 * q] = t.x; vb[4 * q + 1] = t.y; vb[4 * q + 2] = t.z; vb[4 * q + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < TK / 2; ++k) {
+        const int64_t s = sk + k;
+        vb[k] = (row < NT && trow < P && s < S) ? Qm[trow * sr + s * sc] : 0.f;
+      }
     }
   };
   if (nchunks > 0) load_chunk(0);
@@ -420,6 +454,7 @@ cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float
   const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), 1);
   BatchStrides bz;
   bz.sxc = N;
+  bz.vec_m = sc == 1 && vec_rows(Qm, sr, 0) ? 1 : 0;
   count_launch(1);
   kern<<<grid, THREADS, smem, st>>>(map, Qm, sr, sc, X, Y, P, S, N, bz, Aref, errp, xpart,
                                     ypart, status);
@@ -445,6 +480,8 @@ cudaError_t launch_batched_tc(const float *Mm, int64_t sr, int64_t sc, int64_t s
   bz.sxc = sxc;
   bz.sxn = sxn;
   bz.s_total = s_total;
+  bz.vec_x = sxc == 1 && vec_rows(X, sxn, batch > 1 ? sXz : 0) ? 1 : 0;
+  bz.vec_m = sc == 1 && vec_rows(Mm, sr, batch > 1 ? sMz : 0) ? 1 : 0;
   const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), (unsigned)batch);
   count_launch(1);
   mode3_tc_kernel<false><<<grid, THREADS, smem, st>>>(map, Mm, sr, sc, X, Y, P, S, N, bz,
