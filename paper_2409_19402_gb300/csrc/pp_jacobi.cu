@@ -851,9 +851,9 @@ __device__ __noinline__ int grid_cross(float *top, float *bot, float *ntop, floa
 
 constexpr int GRID_MAX_P = 4096;   // slices the device-wide kernel takes (activity flags)
 
-// THREADS = bs * GW: one group of GW lanes per cross pair of a round
+// THREADS >= bs * GW: one group of GW lanes per cross pair of a round
 template <int GW, int CW, int THREADS>
-__global__ void __launch_bounds__(THREADS, 512 / THREADS) jacobi_grid_kernel(JacobiArgs A,
+__global__ void __launch_bounds__(THREADS, 1) jacobi_grid_kernel(JacobiArgs A,
                                                                              int a_pad, int bs,
                                                                              int nb) {
   extern __shared__ __align__(16) float sm[];   // top block | bottom block | 2 bs norms
@@ -949,8 +949,14 @@ __global__ void __launch_bounds__(THREADS, 512 / THREADS) jacobi_grid_kernel(Jac
 }
 
 // Grid-kernel launch shape: one warp per pair, bs = 16 vectors per block (at
-// most half the vectors), 512 threads (one group per block vector in a cross
-// round; the top block held in registers across the cross pass).
+// most half the vectors) on 512 threads, or bs = 20 on 640 threads (one group
+// per block vector in a cross round; the top block held in registers across
+// the cross pass), whichever costs less per sweep: the rounds (nb - 1) times
+// the waves of items a round takes on the resident CTAs times an item's bs^2
+// pair rotations (measured on 512 x 512 slices, an item's time grows like bs^2:
+// the SM is throughput-bound).  p = 10 slices of 512 vectors: bs = 16 gives
+// 160 items a round, two waves on 152 SMs; bs = 20 gives 130, one wave, and the
+// SVD stage goes from 14.2 to 9.8 ms; from p = 25 on, bs = 16 is kept.
 struct GridCfg {
   int GW = 0, CW = 0, bs = 0, nb = 0, grid = 0, threads = 0;
   size_t smem = 0;
@@ -998,13 +1004,26 @@ cudaError_t launch_grid_jacobi(const JacobiArgs &A, int a_pad, cudaStream_t st) 
   g.GW = 32;
   g.CW = n4 <= 128 ? 4 : 6;
   if (n4 > g.GW * g.CW) return cudaErrorInvalidValue;
+  auto blocks = [&](int bs) {
+    int nb = (int)((b + bs - 1) / bs);
+    return nb + (nb & 1);
+  };
+  auto steps = [&](int bs) {   // item steps per sweep, one resident CTA per SM
+    const int nb = blocks(bs);
+    const int64_t items = A.p * (nb / 2);
+    const int64_t waves = (items + num_sms() - 1) / num_sms();
+    return (int64_t)(nb - 1) * waves * bs * bs;
+  };
   g.bs = 16;
   if (g.bs > (b + 1) / 2) g.bs = (int)((b + 1) / 2);
-  g.nb = (int)((b + g.bs - 1) / g.bs);
-  g.nb += g.nb & 1;
+  // the 640-thread shape only where its registers hold the vectors (CW = 4)
+  const bool wide = g.CW == 4 && b >= 40 && 10 * steps(20) < 9 * steps(16);
+  if (wide) g.bs = 20;
+  g.nb = blocks(g.bs);
   g.smem = (size_t)2 * g.bs * a_pad * sizeof(float) + (size_t)2 * g.bs * sizeof(float);
   if ((int64_t)g.smem < b * 4) g.smem = (size_t)b * 4;   // finish_slice: b norms
   // the cross pass needs one group per block vector: THREADS / GW >= bs
+  if (wide) return grid_launch<32, 4, 640>(A, a_pad, g, st);
   return g.CW == 4 ? grid_launch<32, 4, 512>(A, a_pad, g, st)
                    : grid_launch<32, 6, 512>(A, a_pad, g, st);
 }
