@@ -156,6 +156,7 @@ pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUD
 
 struct BwdWs {
   float *Ah, *Bh, *Ch, *Gh, *dAh, *dBh, *part, *dQE, *Sm;
+  int64_t part_floats;
 };
 
 BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p) {
@@ -170,7 +171,8 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
   const int64_t z2 = pp::nt_splits(n, p, n1 * m), z3 = pp::nt_splits(n, p, m * n2);
   if (z2 > z) z = z2;
   if (z3 > z) z = z3;
-  w.part = c.take<float>(z * n * p);
+  w.part_floats = z * n * p;
+  w.part = c.take<float>(w.part_floats);
   w.dQE = c.take<float>(n * p);
   w.Sm = c.take<float>(p * p);
   return w;
@@ -649,7 +651,7 @@ pp_status pprod_backward(const float *A, const float *B, const float *Q, const f
     PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st));
     PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st));
     PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st));
-    if (dQ) PP_TRY(pp::launch_stiefel(Q, dQE, n, p, w.Sm, dQ, st));
+    if (dQ) PP_TRY(pp::launch_stiefel(Q, dQE, n, p, w.Sm, dQ, st, w.part, w.part_floats));
   }
   return PP_OK;
 }

@@ -89,9 +89,28 @@ cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t
 }
 
 cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p, float *Sm,
-                           float *out, cudaStream_t st) {
-  // Sm (p x p) = Q^T D on the tensor cores: M(a, i) = Q[i p + a], X = D (n x p)
-  cudaError_t e = launch_batched_tc(Q, 1, p, 0, D, 0, p, 1, Sm, 0, p, n, p, 1, 0, nullptr, st);
+                           float *out, cudaStream_t st, float *part, int64_t part_floats) {
+  // Sm (p x p) = Q^T D on the tensor cores: M(a, i) = Q[i p + a], X = D (n x p).
+  // One output tile contracted over all n rows is one CTA; with scratch for
+  // the parts, the n rows are split into up to 8 members of at least
+  // max(p, 32) rows (whole 32-row chunks) summed afterwards in a fixed order.
+  int64_t kchunk = (n + 7) / 8;
+  if (kchunk < p) kchunk = p;
+  kchunk = (kchunk + 31) / 32 * 32;
+  const int64_t nz = (n + kchunk - 1) / kchunk;
+  cudaError_t e;
+  if (nz > 1 && part && nz * p * p <= part_floats) {
+    e = launch_batched_tc(Q, 1, p, kchunk * p, D, kchunk * p, p, 1, part, p * p, p, kchunk, p, nz,
+                          n, nullptr, st);
+    if (e != cudaSuccess) return e;
+    int bs = (int)((p * p + 255) / 256);
+    if (bs > 4096) bs = 4096;
+    count_launch(1);
+    sum_parts_kernel<<<bs, 256, 0, st>>>(part, p, p, nz, Sm, 0, 0);
+    e = cudaGetLastError();
+  } else {
+    e = launch_batched_tc(Q, 1, p, 0, D, 0, p, 1, Sm, 0, p, n, p, 1, 0, nullptr, st);
+  }
   if (e != cudaSuccess) return e;
   int b2 = (int)((n * p + 255) / 256);
   if (b2 > 4096) b2 = 4096;

@@ -65,9 +65,11 @@ cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t
 int64_t nt_splits(int64_t R, int64_t S, int64_t K);
 cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
                                  float *part, float *out, int accumulate, cudaStream_t st);
-// out = D - Q sym(Q^T D) for Q, D n x p (Sm: p x p scratch)
+// out = D - Q sym(Q^T D) for Q, D n x p (Sm: p x p scratch; part, of
+// part_floats floats, lets Q^T D split over the n rows)
 cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p, float *Sm,
-                           float *out, cudaStream_t st);
+                           float *out, cudaStream_t st, float *part = nullptr,
+                           int64_t part_floats = 0);
 
 // Batched facewise product C_t = A_t B_t (Def. 2.3).
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
