@@ -83,3 +83,47 @@ def test_batched_cuda_graph_replay(batch):
         k = int(offs[-1])                       # entries past kappa are never written
         assert torch.equal(sv[:k], o.s[:k])
         assert torch.equal(rep, o.rep)
+
+
+def test_batched_every_tensor_sampled_slices_and_ranks(batch):
+    """Every tensor of the batch, at any size: the singular values of its first
+    and last transform-domain slice recomputed one by one by the oracle, each
+    slice's error within 1e-5 of the norm of all the tensor's singular values
+    (the normwise parity tolerance, of which a slice's share is a necessary
+    part; the last slices of these rank-10 tensors hold noise-level values,
+    whose own norm is far below the rounding of the FP32 projection), and the
+    batch's ranks rho equal to the global energy selection (Alg. 4.2 steps
+    4-7, the oracle's) applied to the same kernels' full singular values, bit
+    for bit."""
+    import concurrent.futures as cf
+    import os
+
+    import oracle
+    b = _b()
+    pairs = _dev(batch)
+    B = b.Batch(pairs, GAMMA)
+    outs = B()
+    torch.cuda.synchronize()
+    jobs = []
+    for i, ((A, Q), (Ad, Qd), o) in enumerate(zip(batch, pairs, outs)):
+        assert o.report().status == 0
+        bmin = min(A.shape[1], A.shape[2])
+        full = b.tsvdq_trunc(Ad, Qd, bmin, want_ak=False)
+        torch.cuda.synchronize()
+        sig = full.s.double().cpu().numpy()
+        K, rho, _, _ = oracle.select_energy(sig, GAMMA)
+        assert np.array_equal(o.rho.cpu().numpy(), rho), i
+        assert int(o.offs[-1]) == K, i
+        p = Q.shape[1]
+        for t in sorted({0, p - 1}):
+            jobs.append((i, t, A, Q, sig[t], np.linalg.norm(sig)))
+
+    def one(job):
+        i, t, A, Q, s_gpu, norm_all = job
+        Ah_t = oracle.mode3(A, np.asarray(Q, np.float64)[:, t:t + 1].T)[0]
+        s = oracle.svd(Ah_t)[1]
+        return i, t, np.linalg.norm(s_gpu - s) / max(norm_all, 1e-300)
+
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        for i, t, err in ex.map(one, jobs):
+            assert err <= 1e-5, (i, t, err)
