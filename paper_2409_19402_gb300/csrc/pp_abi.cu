@@ -48,10 +48,19 @@ struct Carve {
 
 constexpr int64_t MAX_LONG_SIDE = 768;   // longest slice side the Jacobi kernel is built for
 
+// scratch for the tf32 image of the mode-3 operand, enough for both
+// directions (Q^T: p x n, Q: n x p)
+size_t mode3_img_max(int64_t n, int64_t p) {
+  const size_t a = pp::mode3_img_bytes(p, n), b = pp::mode3_img_bytes(n, p);
+  return a > b ? a : b;
+}
+
 struct DecompWs {
   float *Ah, *W, *sig, *Ahk;
   int32_t *perm, *sweeps, *status, *rank;
   int32_t *jaux;       // device-wide Jacobi kernel's counters (jacobi_aux_bytes)
+  unsigned char *img;  // tf32 image of Q or Q^T for the mode-3 products (mode3_img_bytes)
+  size_t img_bytes;
   double *kept_p, *disc_p, *part_a, *part_h, *part_e, *scal, *keys;
   int64_t *K;
   // QR preconditioner of the Jacobi SVD (slices that fit its shared memory)
@@ -85,6 +94,8 @@ DecompWs carve_decomp(Carve &c, int64_t l, int64_t m, int64_t n, int64_t p, bool
   w.scal = c.take<double>(8);
   w.status = c.take<int32_t>(1);
   w.jaux = c.take<int32_t>((int64_t)pp::jacobi_aux_bytes(p) / 4);
+  w.img_bytes = mode3_img_max(n, p);
+  w.img = c.take<unsigned char>((int64_t)w.img_bytes);
   w.K = c.take<int64_t>(1);
   if (ragged) {
     w.keys = c.take<double>(p * b);
@@ -157,6 +168,8 @@ pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUD
 struct BwdWs {
   float *Ah, *Bh, *Ch, *Gh, *dAh, *dBh, *part, *dQE, *Sm;
   int64_t part_floats;
+  unsigned char *img;
+  size_t img_bytes;
 };
 
 BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p) {
@@ -175,6 +188,8 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
   w.part = c.take<float>(w.part_floats);
   w.dQE = c.take<float>(n * p);
   w.Sm = c.take<float>(p * p);
+  w.img_bytes = mode3_img_max(n, p);
+  w.img = c.take<unsigned char>((int64_t)w.img_bytes);
   return w;
 }
 
@@ -295,7 +310,7 @@ pp_status project_and_svd(const float *A, const float *Q, int64_t l, int64_t m, 
   // energies |A|^2 and |A-hat|^2 accumulated on the way
   int np_h = 0, np_a = 0;
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, w.Ah, p, n, l * m, nullptr, nullptr, &np_h, w.part_a,
-                             &np_a, w.part_h, w.status, st));
+                             &np_a, w.part_h, w.status, st, w.img, w.img_bytes));
   if (defer) {
     defer->np_a = np_a;
     defer->np_h = np_h;
@@ -344,7 +359,7 @@ pp_status backproject(const float *A, const float *Q, int64_t l, int64_t m, int6
   int np = 0;
   // M(r, c) = Q(r, c) = Q[r*p + c]
   PP_TRY(pp::launch_mode3_tc(Q, p, 1, w.Ahk, Ak, n, p, l * m, A, w.part_e, &np, nullptr, nullptr,
-                             nullptr, w.status, st));
+                             nullptr, w.status, st, w.img, w.img_bytes));
   if (defer)
     defer->np_e = np;
   else
@@ -524,6 +539,7 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
       c.take<float>(sh->p * sh->l * sh->m);
       c.take<float>(sh->p * sh->m * sh->n2);
       c.take<float>(sh->p * sh->l * sh->n2);
+      c.take<unsigned char>((int64_t)mode3_img_max(sh->n, sh->p));
       return c.off;
     case PP_OP_TSVDQ:
     case PP_OP_TSVDQII:
@@ -603,13 +619,15 @@ pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1, int6
   float *Ah = c.take<float>(p * n1 * m);
   float *Bh = c.take<float>(p * m * n2);
   float *Ch = c.take<float>(p * n1 * n2);
+  const size_t img_bytes = mode3_img_max(n, p);
+  unsigned char *img = c.take<unsigned char>((int64_t)img_bytes);
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, Ah, p, n, n1 * m, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st));
+                             nullptr, nullptr, nullptr, st, img, img_bytes));
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, B, Bh, p, n, m * n2, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st));
+                             nullptr, nullptr, nullptr, st, img, img_bytes));
   PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st));
   PP_TRY(pp::launch_mode3_tc(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st));
+                             nullptr, nullptr, nullptr, st, img, img_bytes));
   return PP_OK;
 }
 
@@ -627,11 +645,11 @@ pp_status pprod_backward(const float *A, const float *B, const float *Q, const f
   const BwdWs w = carve_bwd(c, n1, m, n2, n, p);
   auto fwd = [&](const float *X, int64_t pix, float *Y) {   // Y = X x_3 Q^T
     return pp::launch_mode3_tc(Q, 1, p, X, Y, p, n, pix, nullptr, nullptr, nullptr, nullptr,
-                               nullptr, nullptr, nullptr, st);
+                               nullptr, nullptr, nullptr, st, w.img, w.img_bytes);
   };
   auto back = [&](const float *X, int64_t pix, float *Y) {  // Y = X x_3 Q
     return pp::launch_mode3_tc(Q, p, 1, X, Y, n, p, pix, nullptr, nullptr, nullptr, nullptr,
-                               nullptr, nullptr, nullptr, st);
+                               nullptr, nullptr, nullptr, st, w.img, w.img_bytes);
   };
   // recompute the transform-domain operands
   PP_TRY(fwd(A, n1 * m, w.Ah));
@@ -897,7 +915,7 @@ pp_status hosvd_compare(const float *A, const float *Q, int64_t l, int64_t m, in
   {
     int np = 0;
     PP_TRY(pp::launch_mode3_tc(Q, p, 1, w.Ahk, Ak_hosvd, n, p, l * m, A, w.part_e, &np, nullptr,
-                               nullptr, nullptr, w.status, st));
+                               nullptr, nullptr, w.status, st, w.img, w.img_bytes));
     PP_TRY(pp::launch_sum_partials(w.part_e, np, w.scal + 3, st));
   }
   if (rep) {

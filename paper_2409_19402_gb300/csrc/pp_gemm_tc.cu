@@ -39,10 +39,10 @@
 #include <cuda.h>
 
 #include <cstring>
-#include <mutex>
 
 #include "pp_internal.h"
 #include "pp_tc.cuh"
+#include "pp_tma.h"
 
 namespace pp {
 namespace {
@@ -396,50 +396,30 @@ size_t tc_smem(bool tma) {
          1024;
 }
 
-// cuTensorMapEncodeTiled from the driver, looked up once
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled() {
-  static EncodeTiledFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  });
-  return fn;
-}
-
 // The S x N FP32 matrix X as a TMA map with 32 x 128 boxes; false when X's
 // rows are not 16-byte aligned or the driver refuses
 bool make_x_map(const float *X, int64_t S, int64_t N, CUtensorMap *map) {
-  EncodeTiledFn enc = encode_tiled();
-  if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || N % 4 != 0) return false;
-  const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)S};
-  const cuuint64_t strides[1] = {(cuuint64_t)N * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)TM, (cuuint32_t)TK};
-  const cuuint32_t estr[2] = {1, 1};
-  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(X), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_rows_2d(map, X, N, S, (uint32_t)TM, (uint32_t)TK, true);
 }
 
 }  // namespace
 
 int64_t mode3_tc_partials(int64_t P, int64_t N) {
-  return ((N + TM - 1) / TM) * ((P + NT - 1) / NT);
+  // this kernel: one per CTA tile; the warp-specialised one: four per unit
+  // (errp, ypart) and eight per pixel tile (xpart)
+  return ((N + TM - 1) / TM) * ((P + NT - 1) / NT) * 8;
 }
 
 cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
-                            int32_t *status, cudaStream_t st) {
+                            int32_t *status, cudaStream_t st, void *img, size_t img_bytes) {
+  if (img) {
+    bool used = false;
+    cudaError_t e = launch_mode3_ws(Qm, sr, sc, X, Y, P, S, N, Aref, errp, n_partials, xpart,
+                                    n_xpart, ypart, status, img, img_bytes, st, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   if (n_partials) *n_partials = (int)(((N + TM - 1) / TM) * ((P + NT - 1) / NT));
   if (n_xpart) *n_xpart = (int)((N + TM - 1) / TM);
   // TMA for contractions of more than two chunks (two CTAs per SM otherwise)

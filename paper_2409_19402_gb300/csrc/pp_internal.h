@@ -34,11 +34,26 @@ __device__ inline void set_status(int32_t *status, int32_t code) {
 // energy partials: xpart gets *n_xpart sums of X^2 (each X entry counted
 // once), ypart one sum of Y^2 per CTA; partial counts from mode3_tc_partials.
 // A bounded wait that expires writes PP_ETIMEOUT to *status (if non-null).
+// With a scratch buffer img of at least mode3_img_bytes(P, S) bytes (16-byte
+// aligned) and TMA-compatible X, Y, Aref (16-byte aligned, N a multiple of 4)
+// the product runs on the persistent warp-specialised kernel of
+// pp_mode3_ws.cu (one extra launch builds M's tf32 image in img); otherwise on
+// the one-CTA-per-tile kernel.  Both compute the same arithmetic.
 cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
-                            int32_t *status, cudaStream_t st);
+                            int32_t *status, cudaStream_t st, void *img = nullptr,
+                            size_t img_bytes = 0);
+// partial-sum slots for errp, xpart and ypart, enough for either kernel
 int64_t mode3_tc_partials(int64_t P, int64_t N);
+size_t mode3_img_bytes(int64_t P, int64_t S);
+// the warp-specialised kernel; *used = false (nothing launched) when the
+// arguments do not suit it
+cudaError_t launch_mode3_ws(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
+                            int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
+                            int *n_partials, double *xpart, int *n_xpart, double *ypart,
+                            int32_t *status, void *img, size_t img_bytes, cudaStream_t st,
+                            bool *used);
 
 // The same tensor-core product over a batch (grid z): member z computes
 // Y[z] (P x N, row-major) = M[z] (P x S) X[z] (S x N) with M(r, c) =
