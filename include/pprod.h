@@ -362,7 +362,7 @@ PP_API pp_status tsvdqII_batched(const pp_batch_item *items, int64_t count, doub
  * PP_NOALLOC_SCRATCH_BYTES bytes, held on every GPU that loads the library
  * until the process exits.  Shapes whose tsvdqII workspace exceeds it return
  * PP_EWORKSPACE before anything is enqueued (the video-shaped 120 x 160 x 300,
- * p = 50 problem needs about 14.6 MB and fits); argument errors are checked
+ * p = 50 problem needs about 14.8 MB and fits); argument errors are checked
  * first, in tsvdqII's order, and get tsvdqII's status.
  * Every call looks up the array's device address on the current device; the
  * first call on a device may load the library's device module, so make it
