@@ -78,6 +78,10 @@ struct BatchStrides {
   // contraction-contiguous operands with 16-byte aligned rows: a thread's 16
   // consecutive terms come in as four 16-byte loads (register path)
   int vec_x = 0, vec_m = 0;
+  // rz > 0 (register path): grid member z sums the products of members
+  // z rz ... min(nmem, (z + 1) rz) - 1 (operands sMz, sXz apart) into one
+  // output at Y + z sYz, chunk by chunk, in member order
+  int64_t rz = 0, nmem = 0;
 };
 
 // X(c, n) = X[c + n sxn] (sxc = 1) with every member's rows 16-byte aligned
@@ -132,14 +136,20 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // batch member z (blockIdx.z): its operands and output; split-K members
   // (s_total > 0) each take S of the s_total contraction terms, the last fewer
+  int nm = 1;   // members summed by this CTA
   {
     const int64_t z = blockIdx.z;
-    Qm += z * bz.sMz;
-    X += z * bz.sXz;
+    const int64_t m0 = bz.rz > 0 ? z * bz.rz : z;
+    Qm += m0 * bz.sMz;
+    X += m0 * bz.sXz;
     if (Y) Y += z * bz.sYz;
     if (bz.s_total > 0) {
       const int64_t rem = bz.s_total - z * S;
       S = rem < S ? rem : S;
+    }
+    if (bz.rz > 0) {
+      const int64_t left = bz.nmem - m0;
+      nm = (int)(left < bz.rz ? left : bz.rz);
     }
   }
   const int64_t sxc = bz.sxc, sxn = bz.sxn;
@@ -172,7 +182,8 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   for (int j = 0; j < NT / 2; ++j) acc[j] = 0.f;
   const int row = tid & (TM - 1);          // pixel row / slice row owned by this thread
   const int khalf = tid >> 7;              // which 16 of the 32 K values (0 or 1)
-  const int nchunks = (int)((S + TK - 1) / TK);
+  const int nch = (int)((S + TK - 1) / TK);   // chunks per member
+  const int nchunks = nm * nch;
   double xs = 0.0;
   bool ok = true;
   // TMA path: raw FP32 stages after the two converted stages; chunk c goes to
@@ -195,8 +206,14 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   // global-memory latency overlaps the previous chunk's barrier and MMA issue
   const int64_t pix = n0 + row;
   const int64_t trow = y0 + row;
+  const float *const X_ = X, *const Qm_ = Qm;
   float va[TK / 2], vb[TK / 2];
-  auto load_chunk = [&](int c) {
+  auto load_chunk = [&](int cc) {
+    // chunk cc: chunk c of member mem (one member unless the CTA sums several)
+    const int mem = nm > 1 ? cc / nch : 0;
+    const int c = nm > 1 ? cc % nch : cc;
+    const float *X = X_ + mem * bz.sXz;
+    const float *Qm = Qm_ + mem * bz.sMz;
     const int64_t s0 = (int64_t)c * TK;
     const int64_t sk = s0 + khalf * (TK / 2);   // this thread's first term of the chunk
     if (!TMA) {
@@ -467,6 +484,39 @@ cudaError_t launch_batched_tc(const float *Mm, int64_t sr, int64_t sc, int64_t s
   mode3_tc_kernel<false><<<grid, THREADS, smem, st>>>(map, Mm, sr, sc, X, Y, P, S, N, bz,
                                                       nullptr, nullptr, nullptr, nullptr,
                                                       status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_tc(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                             const float *X, int64_t sXz, int64_t sxc, int64_t sxn, float *Y,
+                             int64_t sYz, int64_t P, int64_t S, int64_t N, int64_t nmem,
+                             int64_t groups, cudaStream_t st) {
+  if (nmem < 1 || P < 1 || N < 1 || S < 1) return cudaSuccess;
+  if (groups < 1) groups = 1;
+  if (groups > nmem) groups = nmem;
+  const int64_t rz = (nmem + groups - 1) / groups;
+  groups = (nmem + rz - 1) / rz;   // every group has at least one member
+  if (groups > 65535) return cudaErrorInvalidValue;
+  CUtensorMap map;
+  std::memset(&map, 0, sizeof(map));
+  const size_t smem = tc_smem(false);
+  cudaError_t e = cudaFuncSetAttribute(mode3_tc_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BatchStrides bz;
+  bz.sMz = sMz;
+  bz.sXz = sXz;
+  bz.sYz = sYz;
+  bz.sxc = sxc;
+  bz.sxn = sxn;
+  bz.rz = rz;
+  bz.nmem = nmem;
+  bz.vec_x = sxc == 1 && vec_rows(X, sxn, sXz) ? 1 : 0;
+  bz.vec_m = sc == 1 && vec_rows(Mm, sr, sMz) ? 1 : 0;
+  const dim3 grid((unsigned)((N + TM - 1) / TM), (unsigned)((P + NT - 1) / NT), (unsigned)groups);
+  count_launch(1);
+  mode3_tc_kernel<false><<<grid, THREADS, smem, st>>>(map, Mm, sr, sc, X, Y, P, S, N, bz, nullptr,
+                                                      nullptr, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -65,6 +65,14 @@ cudaError_t launch_batched_tc(const float *Mm, int64_t sr, int64_t sc, int64_t s
                               const float *X, int64_t sXz, int64_t sxc, int64_t sxn, float *Y,
                               int64_t sYz, int64_t P, int64_t S, int64_t N, int64_t batch,
                               int64_t s_total, int32_t *status, cudaStream_t st);
+// Sums of products: Y[g] (P x N) = sum over members z of group g of M[z] X[z]
+// (the same operand layout as launch_batched_tc), nmem members split into at
+// most `groups` groups of consecutive members; each group is one grid layer
+// that accumulates its members' 32-term chunk sums in FP32 in member order.
+cudaError_t launch_reduce_tc(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                             const float *X, int64_t sXz, int64_t sxc, int64_t sxn, float *Y,
+                             int64_t sYz, int64_t P, int64_t S, int64_t N, int64_t nmem,
+                             int64_t groups, cudaStream_t st);
 
 // Batched product Y[z] (P x N) = M[z] (P x S) * X[z] (S x N) (launch_batched_tc), M(r, c) =
 // Mm[z*sMz + r*sr + c*sc], X and Y row-major with leading dimension N; a batch
