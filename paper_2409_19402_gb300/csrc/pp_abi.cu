@@ -189,6 +189,10 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
   w.dQE = c.take<float>(n * p);
   w.Sm = c.take<float>(p * p);
   w.img_bytes = mode3_img_max(n, p);
+  for (int64_t K : {n1 * n2, n1 * m, m * n2}) {   // the three A B^T of the Q gradient
+    const size_t b = pp::nt_img_bytes(n, p, K);
+    if (b > w.img_bytes) w.img_bytes = b;
+  }
   w.img = c.take<unsigned char>((int64_t)w.img_bytes);
   return w;
 }
@@ -666,9 +670,12 @@ pp_status pprod_backward(const float *A, const float *B, const float *Q, const f
   PP_TRY(back(w.dBh, m * n2, dB));
   if (dQ_euclid || dQ) {
     float *dQE = dQ_euclid ? dQ_euclid : w.dQE;
-    PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st));
-    PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st));
-    PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st));
+    PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st, w.img,
+                                    w.img_bytes, w.part_floats));
+    PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st, w.img,
+                                    w.img_bytes, w.part_floats));
+    PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st, w.img,
+                                    w.img_bytes, w.part_floats));
     if (dQ) PP_TRY(pp::launch_stiefel(Q, dQE, n, p, w.Sm, dQ, st, w.part, w.part_floats));
   }
   return PP_OK;

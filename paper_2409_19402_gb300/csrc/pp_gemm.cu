@@ -58,7 +58,23 @@ int64_t nt_splits(int64_t R, int64_t S, int64_t K) {
 }
 
 cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
-                                 float *part, float *out, int accumulate, cudaStream_t st) {
+                                 float *part, float *out, int accumulate, cudaStream_t st,
+                                 void *img, size_t img_bytes, int64_t part_floats) {
+  if (img) {   // the warp-specialised kernel, the smaller operand's tf32 image in img
+    bool used = false, trw = false;
+    int64_t nzw = 0;
+    cudaError_t e = launch_nt_ws(A, B, R, S, K, part, part_floats, img, img_bytes, &nzw, &trw, st,
+                                 &used);
+    if (e != cudaSuccess) return e;
+    if (used) {
+      const int64_t count = R * S;
+      int blocks = (int)((count + 255) / 256);
+      if (blocks > 4096) blocks = 4096;
+      count_launch(1);
+      sum_parts_kernel<<<blocks, 256, 0, st>>>(part, R, S, nzw, out, accumulate, trw ? 1 : 0);
+      return cudaGetLastError();
+    }
+  }
   const int64_t nz = nt_splits(R, S, K);
   int64_t kchunk = (K + nz - 1) / nz;
   kchunk = (kchunk + 31) / 32 * 32;            // whole 32-term chunks per split

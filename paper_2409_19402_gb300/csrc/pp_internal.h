@@ -86,8 +86,19 @@ cudaError_t launch_batched_gemm(const float *Mm, int64_t sr, int64_t sc, int64_t
 // out (R x S) = [out +] A B^T for A (R x K), B (S x K) row-major, split over K into
 // nt_splits(R, S, K) FP32 partials (part) summed in a fixed order.
 int64_t nt_splits(int64_t R, int64_t S, int64_t K);
+// With img (at least nt_img_bytes(R, S, K) bytes) and part_floats of part,
+// the product runs on the warp-specialised kernel (launch_nt_ws).
 cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
-                                 float *part, float *out, int accumulate, cudaStream_t st);
+                                 float *part, float *out, int accumulate, cudaStream_t st,
+                                 void *img = nullptr, size_t img_bytes = 0,
+                                 int64_t part_floats = 0);
+size_t nt_img_bytes(int64_t R, int64_t S, int64_t K);
+// A B^T split over K on the warp-specialised kernel: part[z] for z < *nz_out
+// holds member z's R x S product, or its S x R transpose (*transposed);
+// *used = false (nothing launched) when the arguments do not suit it
+cudaError_t launch_nt_ws(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
+                         float *part, int64_t part_floats, void *img, size_t img_bytes,
+                         int64_t *nz_out, bool *transposed, cudaStream_t st, bool *used);
 // out = D - Q sym(Q^T D) for Q, D n x p (Sm: p x p scratch; part, of
 // part_floats floats, lets Q^T D split over the n rows)
 cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p, float *Sm,

@@ -215,11 +215,17 @@ __global__ void prep_image_kernel(const float *__restrict__ Qm, int64_t sr, int6
   }
 }
 
+// KMAJ: X is contraction-contiguous (X(s, n) = X[n ldx + s]) and comes in as
+// two 128-byte-swizzled 32 x 128 boxes per stage; else X(s, n) = X[s N + n],
+// one unswizzled 128 x 64 box.  The contraction of S terms is split into nz
+// members of kchunk terms (a multiple of KC), member z writing its own
+// P x N product (the third coordinate of the Y map).
+template <bool KMAJ>
 __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
     const __grid_constant__ CUtensorMap amap, const unsigned char *__restrict__ img, int has_y,
-    int has_ref, int P, int S, int N, double *__restrict__ errp, double *__restrict__ xpart,
-    double *__restrict__ ypart, int32_t *status) {
+    int has_ref, int P, int S, int N, int nz, int kchunk, double *__restrict__ errp,
+    double *__restrict__ xpart, double *__restrict__ ypart, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -234,8 +240,18 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tiles_x = (N + TM - 1) / TM, tiles_y = (P + NT - 1) / NT;
-  const int U = tiles_x * tiles_y;
-  const int nst = (S + KC - 1) / KC;
+  const int per = tiles_x * tiles_y;     // units per member
+  const int U = nz * per;
+  const int nst_total = (S + KC - 1) / KC;   // image stages per row tile
+  // unit u: member z, row tile ty (fastest), pixel tile tx; its stages
+  auto unit = [&](int u, int &z, int &ty, int &tx) {
+    z = u / per;
+    const int r = u - z * per;
+    ty = r % tiles_y;
+    tx = r / tiles_y;
+    const int sz = S - z * kchunk;
+    return ((sz < kchunk ? sz : kchunk) + KC - 1) / KC;
+  };
   if (tid == 0) {
     for (int i = 0; i < R; ++i) {
       init_bar(&x_full[i], 1);
@@ -271,14 +287,22 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       int g = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < U; u += gridDim.x) {
-        const int tx = u / tiles_y;
+        int z, ty, tx;
+        const int nst = unit(u, z, ty, tx);
         for (int c = 0; c < nst; ++c, ++g) {
           if (g >= R && !wait_or_abort(smem_u32(&x_empty[xr.i]), xr.ph ^ 1u, &abort_flag)) {
             ok = false;
             break;
           }
-          mbar_expect_tx(smem_u32(&x_full[xr.i]), (uint32_t)RAW);
-          tma_load_2d(smem_u32(xraw + xr.i * RAW), &xmap, tx * TM, c * KC, smem_u32(&x_full[xr.i]));
+          const uint32_t dst = smem_u32(xraw + xr.i * RAW), fb = smem_u32(&x_full[xr.i]);
+          const int s0 = z * kchunk + c * KC;   // first term of the stage
+          mbar_expect_tx(fb, (uint32_t)RAW);
+          if (KMAJ) {
+            tma_load_2d(dst, &xmap, s0, tx * TM, fb);
+            tma_load_2d(dst + RAW / 2, &xmap, s0 + TK, tx * TM, fb);
+          } else {
+            tma_load_2d(dst, &xmap, tx * TM, s0, fb);
+          }
           xr.next(R);
         }
       }
@@ -293,15 +317,17 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       int g = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < U; u += gridDim.x) {
-        const int ty = u % tiles_y;
+        int z, ty, tx;
+        const int nst = unit(u, z, ty, tx);
         for (int c = 0; c < nst; ++c, ++g) {
           if (g >= SB && !wait_or_abort(smem_u32(&b_empty[br.i]), br.ph ^ 1u, &abort_flag)) {
             ok = false;
             break;
           }
           mbar_expect_tx(smem_u32(&b_full[br.i]), (uint32_t)BST);
-          bulk_load(smem_u32(bimg + br.i * BST), img + ((int64_t)ty * nst + c) * BST,
-                    (uint32_t)BST, smem_u32(&b_full[br.i]));
+          const int64_t stage = (int64_t)ty * nst_total + (int64_t)z * (kchunk / KC) + c;
+          bulk_load(smem_u32(bimg + br.i * BST), img + stage * BST, (uint32_t)BST,
+                    smem_u32(&b_full[br.i]));
           br.next(SB);
         }
       }
@@ -319,6 +345,8 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       int g = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < U; u += gridDim.x) {
+        int z, ty, tx;
+        const int nst = unit(u, z, ty, tx);
         for (int c = 0; c < nst; ++c, ++g) {
           if (!wait_or_abort(smem_u32(&a_full[ar.i]), ar.ph, &abort_flag) ||
               !wait_or_abort(smem_u32(&b_full[br.i]), br.ph, &abort_flag) ||
@@ -373,8 +401,9 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     int g = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < U; u += gridDim.x) {
-      const int tx = u / tiles_y;
-      const bool do_x = xpart != nullptr && (u % tiles_y) == 0;
+      int z, ty, tx;
+      const int nst = unit(u, z, ty, tx);
+      const bool do_x = xpart != nullptr && ty == 0 && z == 0;
       double xs = 0.0;
       for (int c = 0; c < nst; ++c, ++g, xr.next(R), ar.next(SA)) {
         if (g % NCG != cg) continue;
@@ -383,12 +412,26 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
           ok = false;
           break;
         }
-        const float *rp = reinterpret_cast<const float *>(xraw + xr.i * RAW);
         float v[32], w[32];
+        if (KMAJ) {
+          // two swizzled 32 x 128 boxes: row `row` holds terms 0-31 (and 32-63 in
+          // the second box) as eight 16-byte chunks, chunk j at j ^ (row mod 8)
+          const unsigned char *rb = xraw + xr.i * RAW + row * 128;
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          v[k] = rp[k * TM + row];
-          w[k] = rp[(32 + k) * TM + row];
+          for (int j = 0; j < 8; ++j) {
+            const uint32_t off = (uint32_t)(((j ^ row) & 7) << 4);
+            const float4 a = *reinterpret_cast<const float4 *>(rb + off);
+            const float4 b = *reinterpret_cast<const float4 *>(rb + RAW / 2 + off);
+            v[4 * j] = a.x; v[4 * j + 1] = a.y; v[4 * j + 2] = a.z; v[4 * j + 3] = a.w;
+            w[4 * j] = b.x; w[4 * j + 1] = b.y; w[4 * j + 2] = b.z; w[4 * j + 3] = b.w;
+          }
+        } else {
+          const float *rp = reinterpret_cast<const float *>(xraw + xr.i * RAW);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            v[k] = rp[k * TM + row];
+            w[k] = rp[(32 + k) * TM + row];
+          }
         }
         __syncwarp();
         if (lane == 0) arrive(smem_u32(&x_empty[xr.i]));
@@ -447,7 +490,8 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     int g = 0, ul = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < U; u += gridDim.x, ++ul) {
-      const int ty = u % tiles_y, tx = u / tiles_y;
+      int z, ty, tx;
+      const int nst = unit(u, z, ty, tx);
       float *stg = reinterpret_cast<float *>(ostg + (warp * OB + (ul % OB)) * OSTG);
       // this staging tile's store from OB units ago has been read; then the
       // reference tile (A) of this unit comes into it by TMA
@@ -516,13 +560,13 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       __syncwarp();
       if (lane == 0 && has_y) {   // out-of-range rows and pixels are clipped by the store
         asm volatile(
-            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
                 reinterpret_cast<uint64_t>(&ymap)),
-            "r"(tx * TM + warp * 32), "r"(ty * NT), "r"(smem_u32(stg))
+            "r"(tx * TM + warp * 32), "r"(ty * NT), "r"(z), "r"(smem_u32(stg))
             : "memory");
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
-      const int64_t part = ((int64_t)ty * tiles_x + tx) * 4 + warp;
+      const int64_t part = (((int64_t)z * tiles_y + ty) * tiles_x + tx) * 4 + warp;
       if (errp) {
         for (int off = 16; off > 0; off >>= 1) err += __shfl_xor_sync(0xffffffffu, err, off);
         if (lane == 0) errp[part] = err;
@@ -558,6 +602,46 @@ int64_t mode3_ws_partials(int64_t P, int64_t N) {
   return ((N + TM - 1) / TM) * ((P + NT - 1) / NT) * 4;
 }
 
+namespace {
+
+// The image of M (P x S, M(r, c) = Qm[r sr + c sc]) and one launch of the
+// kernel over nz members of kchunk terms; Y, when given, a 3-D map of nz
+// P x N products.
+template <bool KMAJ>
+cudaError_t run_ws(const CUtensorMap &xmap, const CUtensorMap &ymap, const CUtensorMap &amap,
+                   const float *Qm, int64_t sr, int64_t sc, bool has_y, bool has_ref, int64_t P,
+                   int64_t S, int64_t N, int64_t nz, int64_t kchunk, double *errp,
+                   double *xpart, double *ypart, int32_t *status, void *img, cudaStream_t st) {
+  const int64_t tiles_y = (P + NT - 1) / NT, nst = (S + KC - 1) / KC, tiles_x = (N + TM - 1) / TM;
+  const int64_t total = tiles_y * 2 * nst * NT * 8;
+  int pb = (int)((total + 255) / 256);
+  if (pb > 4 * num_sms()) pb = 4 * num_sms();
+  count_launch(1);
+  prep_image_kernel<<<pb, 256, 0, st>>>(Qm, sr, sc, P, S, 2 * nst, tiles_y,
+                                        static_cast<unsigned char *>(img));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t U = nz * tiles_x * tiles_y;
+  const int grid = (int)(U < num_sms() ? U : num_sms());
+  count_launch(1);
+  mode3_ws_kernel<KMAJ><<<grid, THREADS, SMEM_BYTES, st>>>(
+      xmap, ymap, amap, static_cast<const unsigned char *>(img), has_y ? 1 : 0, has_ref ? 1 : 0,
+      (int)P, (int)S, (int)N, (int)nz, (int)kchunk, errp, xpart, ypart, status);
+  return cudaGetLastError();
+}
+
+template <bool KMAJ>
+bool ws_attr() {
+  if (cudaFuncSetAttribute(mode3_ws_kernel<KMAJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)SMEM_BYTES) != cudaSuccess) {
+    (void)cudaGetLastError();   // this device cannot host it: the caller takes the other kernel
+    return false;
+  }
+  return true;
+}
+
+}  // namespace
+
 cudaError_t launch_mode3_ws(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
@@ -573,34 +657,59 @@ cudaError_t launch_mode3_ws(const float *Qm, int64_t sr, int64_t sc, const float
   std::memset(&ymap, 0, sizeof(ymap));
   std::memset(&amap, 0, sizeof(amap));
   if (!encode_rows_2d(&xmap, X, N, S, (uint32_t)TM, (uint32_t)KC, true)) return cudaSuccess;
-  if (Y && !encode_rows_2d(&ymap, Y, N, P, 32u, (uint32_t)NT, false)) return cudaSuccess;
+  if (Y && !encode_layers_3d(&ymap, Y, N, P, 1, 32u, (uint32_t)NT)) return cudaSuccess;
   if (Aref && !encode_rows_2d(&amap, Aref, N, P, 32u, (uint32_t)NT, false)) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(mode3_ws_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)SMEM_BYTES);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();   // this device cannot host it: the caller takes the other kernel
-    return cudaSuccess;
-  }
+  if (!ws_attr<false>()) return cudaSuccess;
   *used = true;
-  const int64_t tiles_y = (P + NT - 1) / NT, nst = (S + KC - 1) / KC, tiles_x = (N + TM - 1) / TM;
+  const int64_t tiles_y = (P + NT - 1) / NT, tiles_x = (N + TM - 1) / TM;
   if (n_partials) *n_partials = (int)(tiles_x * tiles_y * 4);
   if (n_xpart) *n_xpart = (int)(tiles_x * NCG * 4);
-  const int64_t total = tiles_y * 2 * nst * NT * 8;
-  int pb = (int)((total + 255) / 256);
-  if (pb > 4 * num_sms()) pb = 4 * num_sms();
-  count_launch(1);
-  prep_image_kernel<<<pb, 256, 0, st>>>(Qm, sr, sc, P, S, 2 * nst, tiles_y,
-                                        static_cast<unsigned char *>(img));
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t U = tiles_x * tiles_y;
-  const int grid = (int)(U < num_sms() ? U : num_sms());
-  count_launch(1);
-  mode3_ws_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(
-      xmap, ymap, amap, static_cast<const unsigned char *>(img), Y ? 1 : 0, Aref ? 1 : 0, (int)P,
-      (int)S, (int)N, Aref ? errp : nullptr, xpart, ypart, status);
-  return cudaGetLastError();
+  const int64_t kchunk = (S + KC - 1) / KC * KC;   // one member: the whole contraction
+  return run_ws<false>(xmap, ymap, amap, Qm, sr, sc, Y != nullptr, Aref != nullptr, P, S, N, 1,
+                       kchunk, Aref ? errp : nullptr, xpart, ypart, status, img, st);
+}
+
+size_t nt_img_bytes(int64_t R, int64_t S, int64_t K) {
+  return mode3_img_bytes(S < R ? S : R, K);
+}
+
+cudaError_t launch_nt_ws(const float *A, const float *B, int64_t R, int64_t S, int64_t K,
+                         float *part, int64_t part_floats, void *img, size_t img_bytes,
+                         int64_t *nz_out, bool *transposed, cudaStream_t st, bool *used) {
+  *used = false;
+  // part[z] = A[:, z kc ..] B[:, z kc ..]^T (R x S), or its transpose B A^T (S x R) when
+  // S < R, so that the larger side runs along the 128-row MMA tiles; M = first, X = second
+  const bool tr = S < R;
+  const float *first = tr ? B : A, *second = tr ? A : B;
+  const int64_t P = tr ? S : R, N = tr ? R : S;
+  if (!img || !part || img_bytes < mode3_img_bytes(P, K) || K < 1 || P < 1 || N < 1 ||
+      K > ((int64_t)1 << 30) || N > ((int64_t)1 << 30) || K % 4 != 0 ||
+      (reinterpret_cast<uintptr_t>(img) & 15) != 0)
+    return cudaSuccess;
+  // members: about one unit per SM, each at least four stages
+  const int64_t per = ((N + TM - 1) / TM) * ((P + NT - 1) / NT);
+  int64_t nz = (num_sms() + per - 1) / per;
+  const int64_t zmax = (K + 4 * KC - 1) / (4 * KC);
+  if (nz > zmax) nz = zmax;
+  if (nz < 1) nz = 1;
+  int64_t kchunk = (K + nz - 1) / nz;
+  kchunk = (kchunk + KC - 1) / KC * KC;
+  nz = (K + kchunk - 1) / kchunk;
+  if (nz * R * S > part_floats || nz > 65535) return cudaSuccess;
+  CUtensorMap xmap, ymap, amap;
+  std::memset(&xmap, 0, sizeof(xmap));
+  std::memset(&ymap, 0, sizeof(ymap));
+  std::memset(&amap, 0, sizeof(amap));
+  // X(s, n) = second[n K + s]: rows of K terms, 32 x 128 boxes with the 128-byte swizzle
+  if (!encode_rows_2d(&xmap, second, K, N, (uint32_t)TK, (uint32_t)TM, true, true))
+    return cudaSuccess;
+  if (!encode_layers_3d(&ymap, part, N, P, nz, 32u, (uint32_t)NT)) return cudaSuccess;
+  if (!ws_attr<true>()) return cudaSuccess;
+  *used = true;
+  *nz_out = nz;
+  *transposed = tr;
+  return run_ws<true>(xmap, ymap, amap, first, K, 1, true, false, P, K, N, nz, kchunk, nullptr,
+                      nullptr, nullptr, nullptr, img, st);
 }
 
 }  // namespace pp

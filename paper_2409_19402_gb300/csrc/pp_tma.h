@@ -35,7 +35,8 @@ inline EncodeTiledFn encode_tiled() {
 // elements read as zero and clipped on stores.  False when the base is not
 // 16-byte aligned, a row is not a multiple of 16 bytes, or the driver refuses.
 inline bool encode_rows_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
-                           uint32_t box_inner, uint32_t box_outer, bool l2_promote) {
+                           uint32_t box_inner, uint32_t box_outer, bool l2_promote,
+                           bool swizzle128 = false) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || inner % 4 != 0 || inner < 1 ||
       outer < 1)
@@ -45,9 +46,28 @@ inline bool encode_rows_2d(CUtensorMap *map, const float *base, int64_t inner, i
   const cuuint32_t box[2] = {box_inner, box_outer};
   const cuuint32_t estr[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
-             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
              l2_promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// `layers` row-major outer x inner FP32 matrices, one after the other, as a
+// 3-D map with box_outer x box_inner x 1 boxes, no swizzle (clipped per layer).
+inline bool encode_layers_3d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
+                             int64_t layers, uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || inner % 4 != 0 || inner < 1 ||
+      outer < 1 || layers < 1)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)layers};
+  const cuuint64_t strides[2] = {(cuuint64_t)inner * sizeof(float),
+                                 (cuuint64_t)(inner * outer) * sizeof(float)};
+  const cuuint32_t box[3] = {box_inner, box_outer, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace pp
