@@ -13,16 +13,43 @@ namespace {
 
 // ---------------------------------------------------------------- A B^T, split over K
 // out (R x S) (+)= sum over z of part[z], in z order; the parts hold R x S
-// (transposed = 0) or S x R (transposed = 1) products
-__global__ void sum_parts_kernel(const float *__restrict__ part, int64_t R, int64_t S, int64_t nz,
-                                 float *__restrict__ out, int accumulate, int transposed) {
+// (transposed = 0) or S x R (transposed = 1) products.  One CTA of 1024
+// threads per 32 x 32 tile of the parts, one entry per thread summed over z
+// with the parts read along their rows; a transposed tile goes out through
+// shared memory so that the writes run along out's rows as well.
+__global__ void __launch_bounds__(1024) sum_parts_kernel(const float *__restrict__ part,
+                                                         int64_t R, int64_t S, int64_t nz,
+                                                         float *__restrict__ out, int accumulate,
+                                                         int transposed) {
+  __shared__ float tile[32][33];
   const int64_t count = R * S;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t src = transposed ? (e % S) * R + e / S : e;
-    float s = accumulate ? out[e] : 0.f;
-    for (int64_t z = 0; z < nz; ++z) s += part[z * count + src];
-    out[e] = s;
+  // the parts are rows x cols: S x R when transposed, else R x S
+  const int64_t rows = transposed ? S : R, cols = transposed ? R : S;
+  const int64_t tiles_c = (cols + 31) / 32;
+  const int64_t r0 = (int64_t)(blockIdx.x / tiles_c) * 32, c0 = (int64_t)(blockIdx.x % tiles_c) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t r = r0 + ty, c = c0 + tx;
+  float v = 0.f;
+  if (r < rows && c < cols) {
+    const float *pz = part + r * cols + c;
+#pragma unroll 8
+    for (int64_t z = 0; z < nz; ++z) v += pz[z * count];   // fixed order
+  }
+  if (!transposed) {
+    if (r < rows && c < cols) {
+      const int64_t e = r * cols + c;
+      out[e] = accumulate ? out[e] + v : v;
+    }
+    return;
+  }
+  tile[ty][tx] = v;
+  __syncthreads();
+  // out (R x S): out row = part column, out column = part row
+  const int64_t oc = c0 + ty, orow = r0 + tx;   // part column c0 + ty, part row r0 + tx
+  if (orow < rows && oc < cols) {
+    const int64_t e = oc * S + orow;
+    const float w = tile[tx][ty];
+    out[e] = accumulate ? out[e] + w : w;
   }
 }
 
@@ -37,6 +64,11 @@ __global__ void stiefel_kernel(const float *__restrict__ Q, const float *__restr
     for (int64_t a = 0; a < p; ++a) s = fmaf(Q[i * p + a], 0.5f * (Sm[a * p + b] + Sm[b * p + a]), s);
     out[e] = D[e] - s;
   }
+}
+
+// one CTA per 32 x 32 tile of the R x S output
+unsigned sum_parts_blocks(int64_t R, int64_t S) {
+  return (unsigned)(((R + 31) / 32) * ((S + 31) / 32));
 }
 
 }  // namespace
@@ -67,11 +99,9 @@ cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int6
                                  &used);
     if (e != cudaSuccess) return e;
     if (used) {
-      const int64_t count = R * S;
-      int blocks = (int)((count + 255) / 256);
-      if (blocks > 4096) blocks = 4096;
       count_launch(1);
-      sum_parts_kernel<<<blocks, 256, 0, st>>>(part, R, S, nzw, out, accumulate, trw ? 1 : 0);
+      sum_parts_kernel<<<sum_parts_blocks(R, S), 1024, 0, st>>>(part, R, S, nzw, out, accumulate,
+                                                                trw ? 1 : 0);
       return cudaGetLastError();
     }
   }
@@ -87,11 +117,9 @@ cudaError_t launch_nt_accumulate(const float *A, const float *B, int64_t R, int6
   cudaError_t e = launch_batched_tc(first, K, 1, kchunk, second, kchunk, 1, K, part, R * S, P,
                                     kchunk, N, nzu, K, nullptr, st);
   if (e != cudaSuccess) return e;
-  const int64_t count = R * S;
-  int blocks = (int)((count + 255) / 256);
-  if (blocks > 4096) blocks = 4096;
   count_launch(1);
-  sum_parts_kernel<<<blocks, 256, 0, st>>>(part, R, S, nzu, out, accumulate, tr ? 1 : 0);
+  sum_parts_kernel<<<sum_parts_blocks(R, S), 1024, 0, st>>>(part, R, S, nzu, out, accumulate,
+                                                            tr ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -119,10 +147,8 @@ cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p,
     e = launch_batched_tc(Q, 1, p, kchunk * p, D, kchunk * p, p, 1, part, p * p, p, kchunk, p, nz,
                           n, nullptr, st);
     if (e != cudaSuccess) return e;
-    int bs = (int)((p * p + 255) / 256);
-    if (bs > 4096) bs = 4096;
     count_launch(1);
-    sum_parts_kernel<<<bs, 256, 0, st>>>(part, p, p, nz, Sm, 0, 0);
+    sum_parts_kernel<<<sum_parts_blocks(p, p), 1024, 0, st>>>(part, p, p, nz, Sm, 0, 0);
     e = cudaGetLastError();
   } else {
     e = launch_batched_tc(Q, 1, p, 0, D, 0, p, 1, Sm, 0, p, n, p, 1, 0, nullptr, st);
