@@ -2,7 +2,9 @@
 // warp-specialised tcgen05 kernel: Y (P x N) = M (P x S) X (S x N) over the
 // mode-3 unfolding, N = l m pixels, for the transform A x_3 Q^T of Alg. 4.1
 // step 2 and the reverse transform x_3 Q of step 4 when the caller provides a
-// small scratch buffer for M's converted image.
+// small scratch buffer for M's converted image; and, with X contraction-
+// contiguous and the contraction split into members, the A B^T over all
+// pixels of the Q gradient (launch_nt_ws).
 //
 // Arithmetic (the same as the one-CTA-per-tile kernel of pp_gemm_tc.cu): the
 // 3-pass split tf32 product hi.hi + hi.lo + lo.hi with hi = tf32(x) and
@@ -19,8 +21,10 @@
 // run at the same time share a pixel tile of X through L2).  Each unit runs
 // over S in stages of KC = 64 terms.  The roles, tied together by mbarrier
 // rings whose every wait is bounded:
-//   - producer warp: one TMA box per stage, X rows [64 c, 64 c + 64) x the
-//     unit's 128 pixels, FP32 and unswizzled, into a ring of R raw stages;
+//   - producer warp: per stage, X's terms [64 c, 64 c + 64) for the unit's 128
+//     pixels into a ring of R raw stages: one unswizzled 128 x 64 box when X
+//     is pixel-contiguous, two 128-byte-swizzled 32 x 128 boxes when it is
+//     contraction-contiguous;
 //   - image warp: one bulk copy per stage of the hi/lo image of M (two
 //     32-wide chunks, K-major, 128-byte swizzle: the MMA's B operand), built
 //     once per call by prep_image_kernel, into a ring of SB stages;
