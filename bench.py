@@ -915,11 +915,20 @@ def main():
     ap.add_argument("--no-diff", action="store_true", help="skip the differentiation step run")
     ap.add_argument("--no-hyperspectral", action="store_true",
                     help="skip the hyperspectral-shaped runs")
+    ap.add_argument("--diff-only", action="store_true",
+                    help="run only the differentiation step and print its timing (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.diff_only:
+        import torch
+        import __graft_entry__
+        __graft_entry__.build()
+        dev = torch.device("cuda:0")
+        print(json.dumps(run_diff(args, torch, torch.cuda.Stream(), dev)))
+        return 0
     return run_ours(args)
 
 
