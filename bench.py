@@ -712,11 +712,31 @@ def run_diff(args, torch, stream, dev):
         e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    eager_loss = float(loss.detach())
+    # the same step captured once as a CUDA graph (forward, loss and backward)
+    # and replayed: the GPU time without the host's per-launch cost
+    gph = torch.cuda.CUDAGraph()
+    W.grad = X.grad = Q.grad = None
+    with torch.cuda.graph(gph, stream=stream):
+        static_loss = 0.5 * ((ag.qprod(W, X, Q) - T) ** 2).sum()
+        static_loss.backward()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            gph.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            gph.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1) / args.steps
     n, n1, m, n2, p = 512, 256, 256, 64, 64
     flops = 2.0 * (n * p * (n1 * m + m * n2) + p * n1 * m * n2 + n * p * n1 * n2)  # forward
     return {"shapes": "W 256x256x512, X 256x64x512, Q 512x64", "ms_fwd_bwd": ms,
-            "loss": float(loss.detach()), "forward_flops": flops,
-            "note": "includes the torch loss/residual ops; all products in the library"}
+            "ms_fwd_bwd_graph": ms_graph, "loss": eager_loss,
+            "loss_graph": float(static_loss.detach()), "forward_flops": flops,
+            "note": "includes the torch loss/residual ops; all products in the library; "
+                    "_graph: the step replayed as one CUDA graph"}
 
 
 def run_batched(args, torch, binding, stream, dev):

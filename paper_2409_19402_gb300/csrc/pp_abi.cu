@@ -55,6 +55,26 @@ size_t mode3_img_max(int64_t n, int64_t p) {
   return a > b ? a : b;
 }
 
+// The projected product's images: Q^T (p x n) and Q (n x p), each built once
+// per call and kept for all of its transforms, and one region for the other
+// products (facewise and, in the backward, the A B^T of the Q gradient).
+struct PprodImg {
+  unsigned char *qt, *q, *other;
+  size_t qt_bytes, q_bytes, other_bytes;
+  bool qt_ready = false, q_ready = false;
+};
+
+PprodImg carve_pprod_img(Carve &c, int64_t n, int64_t p, size_t other_bytes) {
+  PprodImg g;
+  g.qt_bytes = pp::mode3_img_bytes(p, n);
+  g.q_bytes = pp::mode3_img_bytes(n, p);
+  g.other_bytes = other_bytes;
+  g.qt = c.take<unsigned char>((int64_t)g.qt_bytes);
+  g.q = c.take<unsigned char>((int64_t)g.q_bytes);
+  g.other = c.take<unsigned char>((int64_t)other_bytes);
+  return g;
+}
+
 struct DecompWs {
   float *Ah, *W, *sig, *Ahk;
   int32_t *perm, *sweeps, *status, *rank;
@@ -168,8 +188,7 @@ pp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PP_OK : PP_ECUD
 struct BwdWs {
   float *Ah, *Bh, *Ch, *Gh, *dAh, *dBh, *part, *dQE, *Sm;
   int64_t part_floats;
-  unsigned char *img;
-  size_t img_bytes;
+  PprodImg img;
 };
 
 BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p) {
@@ -188,12 +207,15 @@ BwdWs carve_bwd(Carve &c, int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t 
   w.part = c.take<float>(w.part_floats);
   w.dQE = c.take<float>(n * p);
   w.Sm = c.take<float>(p * p);
-  w.img_bytes = mode3_img_max(n, p);
+  size_t other = pp::facewise_img_bytes(n1, m, n2, p);
   for (int64_t K : {n1 * n2, n1 * m, m * n2}) {   // the three A B^T of the Q gradient
     const size_t b = pp::nt_img_bytes(n, p, K);
-    if (b > w.img_bytes) w.img_bytes = b;
+    if (b > other) other = b;
   }
-  w.img = c.take<unsigned char>((int64_t)w.img_bytes);
+  // the facewise dA-hat_t = G-hat_t B-hat_t^T and dB-hat_t = A-hat_t^T G-hat_t
+  for (size_t b : {pp::facewise_img_bytes(n1, n2, m, p), pp::facewise_img_bytes(m, n1, n2, p)})
+    if (b > other) other = b;
+  w.img = carve_pprod_img(c, n, p, other);
   return w;
 }
 
@@ -543,7 +565,7 @@ size_t pp_workspace_bytes(int32_t op, const pp_shape *sh) {
       c.take<float>(sh->p * sh->l * sh->m);
       c.take<float>(sh->p * sh->m * sh->n2);
       c.take<float>(sh->p * sh->l * sh->n2);
-      c.take<unsigned char>((int64_t)mode3_img_max(sh->n, sh->p));
+      carve_pprod_img(c, sh->n, sh->p, pp::facewise_img_bytes(sh->l, sh->m, sh->n2, sh->p));
       return c.off;
     case PP_OP_TSVDQ:
     case PP_OP_TSVDQII:
@@ -623,15 +645,14 @@ pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1, int6
   float *Ah = c.take<float>(p * n1 * m);
   float *Bh = c.take<float>(p * m * n2);
   float *Ch = c.take<float>(p * n1 * n2);
-  const size_t img_bytes = mode3_img_max(n, p);
-  unsigned char *img = c.take<unsigned char>((int64_t)img_bytes);
+  PprodImg g = carve_pprod_img(c, n, p, pp::facewise_img_bytes(n1, m, n2, p));
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, A, Ah, p, n, n1 * m, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st, img, img_bytes));
+                             nullptr, nullptr, nullptr, st, g.qt, g.qt_bytes, &g.qt_ready));
   PP_TRY(pp::launch_mode3_tc(Q, 1, p, B, Bh, p, n, m * n2, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st, img, img_bytes));
-  PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st));
+                             nullptr, nullptr, nullptr, st, g.qt, g.qt_bytes, &g.qt_ready));
+  PP_TRY(pp::launch_facewise_gemm(Ah, Bh, Ch, n1, m, n2, p, st, g.other, g.other_bytes));
   PP_TRY(pp::launch_mode3_tc(Q, p, 1, Ch, C, n, p, n1 * n2, nullptr, nullptr, nullptr, nullptr,
-                             nullptr, nullptr, nullptr, st, img, img_bytes));
+                             nullptr, nullptr, nullptr, st, g.q, g.q_bytes, &g.q_ready));
   return PP_OK;
 }
 
@@ -646,36 +667,37 @@ pp_status pprod_backward(const float *A, const float *B, const float *Q, const f
   if (pp_status e = check_ws(ws, ws_bytes, pp_workspace_bytes(PP_OP_PPROD_BWD, &sh))) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Carve c(ws);
-  const BwdWs w = carve_bwd(c, n1, m, n2, n, p);
+  BwdWs w = carve_bwd(c, n1, m, n2, n, p);
+  PprodImg &g = w.img;
   auto fwd = [&](const float *X, int64_t pix, float *Y) {   // Y = X x_3 Q^T
     return pp::launch_mode3_tc(Q, 1, p, X, Y, p, n, pix, nullptr, nullptr, nullptr, nullptr,
-                               nullptr, nullptr, nullptr, st, w.img, w.img_bytes);
+                               nullptr, nullptr, nullptr, st, g.qt, g.qt_bytes, &g.qt_ready);
   };
   auto back = [&](const float *X, int64_t pix, float *Y) {  // Y = X x_3 Q
     return pp::launch_mode3_tc(Q, p, 1, X, Y, n, p, pix, nullptr, nullptr, nullptr, nullptr,
-                               nullptr, nullptr, nullptr, st, w.img, w.img_bytes);
+                               nullptr, nullptr, nullptr, st, g.q, g.q_bytes, &g.q_ready);
   };
   // recompute the transform-domain operands
   PP_TRY(fwd(A, n1 * m, w.Ah));
   PP_TRY(fwd(B, m * n2, w.Bh));
-  PP_TRY(pp::launch_facewise_gemm(w.Ah, w.Bh, w.Ch, n1, m, n2, p, st));
+  PP_TRY(pp::launch_facewise_gemm(w.Ah, w.Bh, w.Ch, n1, m, n2, p, st, g.other, g.other_bytes));
   PP_TRY(fwd(G, n1 * n2, w.Gh));
-  // dA-hat_t (n1 x m) = G-hat_t (n1 x n2) B-hat_t^T: X(c = j, n = l) = B-hat_t[l*n2 + j]
-  PP_TRY(pp::launch_batched_gemm(w.Gh, n2, 1, n1 * n2, w.Bh, m * n2, w.dAh, n1 * m, n1, n2, m, p,
-                                 st, 1, n2));
-  // dB-hat_t (m x n2) = A-hat_t^T (m x n1) G-hat_t: M(r = l, c = i) = A-hat_t[i*m + l]
-  PP_TRY(pp::launch_batched_gemm(w.Ah, 1, m, n1 * m, w.Gh, n1 * n2, w.dBh, m * n2, m, n1, n2, p,
-                                 st));
+  // dA-hat_t (n1 x m) = G-hat_t (n1 x n2) B-hat_t^T: R_t(k = j, l) = B-hat_t[l*n2 + j]
+  PP_TRY(pp::launch_facewise_strided(w.Gh, n2, 1, n1 * n2, w.Bh, 1, n2, m * n2, w.dAh, n1, n2, m,
+                                     p, st, g.other, g.other_bytes));
+  // dB-hat_t (m x n2) = A-hat_t^T (m x n1) G-hat_t: L_t(l, k = i) = A-hat_t[i*m + l]
+  PP_TRY(pp::launch_facewise_strided(w.Ah, 1, m, n1 * m, w.Gh, n2, 1, n1 * n2, w.dBh, m, n1, n2,
+                                     p, st, g.other, g.other_bytes));
   PP_TRY(back(w.dAh, n1 * m, dA));
   PP_TRY(back(w.dBh, m * n2, dB));
   if (dQ_euclid || dQ) {
     float *dQE = dQ_euclid ? dQ_euclid : w.dQE;
-    PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st, w.img,
-                                    w.img_bytes, w.part_floats));
-    PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st, w.img,
-                                    w.img_bytes, w.part_floats));
-    PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st, w.img,
-                                    w.img_bytes, w.part_floats));
+    PP_TRY(pp::launch_nt_accumulate(G, w.Ch, n, p, n1 * n2, w.part, dQE, 0, st, g.other,
+                                    g.other_bytes, w.part_floats));
+    PP_TRY(pp::launch_nt_accumulate(A, w.dAh, n, p, n1 * m, w.part, dQE, 1, st, g.other,
+                                    g.other_bytes, w.part_floats));
+    PP_TRY(pp::launch_nt_accumulate(B, w.dBh, n, p, m * n2, w.part, dQE, 1, st, g.other,
+                                    g.other_bytes, w.part_floats));
     if (dQ) PP_TRY(pp::launch_stiefel(Q, dQE, n, p, w.Sm, dQ, st, w.part, w.part_floats));
   }
   return PP_OK;

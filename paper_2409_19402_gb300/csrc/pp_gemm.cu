@@ -161,11 +161,57 @@ cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p,
   return cudaGetLastError();
 }
 
+size_t facewise_img_bytes(int64_t rows, int64_t inner, int64_t cols, int64_t p) {
+  const size_t face = batched_img_bytes(rows > cols ? cols : rows, inner, 1);
+  const size_t total = face * (size_t)(p < 1 ? 0 : p);
+  const size_t cap = face > FACEWISE_IMG_CAP ? face : FACEWISE_IMG_CAP;
+  return total < cap ? total : cap;
+}
+
+cudaError_t launch_facewise_strided(const float *L, int64_t sLi, int64_t sLk, int64_t sLz,
+                                    const float *Rm, int64_t sRk, int64_t sRj, int64_t sRz,
+                                    float *C, int64_t rows, int64_t inner, int64_t cols,
+                                    int64_t p, cudaStream_t st, void *img, size_t img_bytes) {
+  const size_t face = batched_img_bytes(rows > cols ? cols : rows, inner, 1);
+  int64_t t0 = 0;   // faces before t0 are done
+  if (img && face > 0 && img_bytes >= face) {
+    // the faces in groups whose images fit in img; the larger of rows and
+    // cols along the 128-row MMA tiles (rows: C_t^T = R_t^T L_t^T, C stored
+    // transposed)
+    const int64_t per = (int64_t)(img_bytes / face);
+    for (; t0 < p; t0 += per) {
+      const int64_t nb = p - t0 < per ? p - t0 : per;
+      bool used = false;
+      cudaError_t e = cudaSuccess;
+      if (rows > cols) {
+        const bool mn = sLi == 1, km = !mn && sLk == 1;
+        if (mn || km)
+          e = launch_batched_ws(Rm + t0 * sRz, sRj, sRk, sRz, L + t0 * sLz, sLz, mn ? sLk : sLi,
+                                km, C + t0 * rows * cols, rows * cols, cols, true, cols, inner,
+                                rows, nb, img, img_bytes, st, &used);
+      } else {
+        const bool mn = sRj == 1, km = !mn && sRk == 1;
+        if (mn || km)
+          e = launch_batched_ws(L + t0 * sLz, sLi, sLk, sLz, Rm + t0 * sRz, sRz, mn ? sRk : sRj,
+                                km, C + t0 * rows * cols, rows * cols, cols, false, rows, inner,
+                                cols, nb, img, img_bytes, st, &used);
+      }
+      if (e != cudaSuccess) return e;
+      if (!used) break;
+    }
+    if (t0 >= p) return cudaSuccess;
+  }
+  return launch_batched_tc(L + t0 * sLz, sLi, sLk, sLz, Rm + t0 * sRz, sRz, sRk, sRj,
+                           C + t0 * rows * cols, rows * cols, rows, inner, cols, p - t0, 0,
+                           nullptr, st);
+}
+
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
-                                 int64_t m, int64_t n2, int64_t p, cudaStream_t st) {
+                                 int64_t m, int64_t n2, int64_t p, cudaStream_t st, void *img,
+                                 size_t img_bytes) {
   // slice t: C_t (n1 x n2) = A_t (n1 x m) * B_t (m x n2); A_t(r, c) = A[t*n1*m + r*m + c]
-  return launch_batched_tc(A, m, 1, n1 * m, B, m * n2, n2, 1, C, n1 * n2, n1, m, n2, p, 0, nullptr,
-                           st);
+  return launch_facewise_strided(A, m, 1, n1 * m, B, n2, 1, m * n2, C, n1, m, n2, p, st, img,
+                                 img_bytes);
 }
 
 }  // namespace pp

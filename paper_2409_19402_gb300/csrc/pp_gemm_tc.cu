@@ -430,11 +430,12 @@ int64_t mode3_tc_partials(int64_t P, int64_t N) {
 cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
-                            int32_t *status, cudaStream_t st, void *img, size_t img_bytes) {
+                            int32_t *status, cudaStream_t st, void *img, size_t img_bytes,
+                            bool *img_ready) {
   if (img) {
     bool used = false;
     cudaError_t e = launch_mode3_ws(Qm, sr, sc, X, Y, P, S, N, Aref, errp, n_partials, xpart,
-                                    n_xpart, ypart, status, img, img_bytes, st, &used);
+                                    n_xpart, ypart, status, img, img_bytes, st, &used, img_ready);
     if (used || e != cudaSuccess) return e;
   }
   if (n_partials) *n_partials = (int)(((N + TM - 1) / TM) * ((P + NT - 1) / NT));

@@ -38,12 +38,14 @@ __device__ inline void set_status(int32_t *status, int32_t code) {
 // aligned) and TMA-compatible X, Y, Aref (16-byte aligned, N a multiple of 4)
 // the product runs on the persistent warp-specialised kernel of
 // pp_mode3_ws.cu (one extra launch builds M's tf32 image in img); otherwise on
-// the one-CTA-per-tile kernel.  Both compute the same arithmetic.
+// the one-CTA-per-tile kernel.  Both compute the same arithmetic.  img_ready
+// (optional): true on entry when img already holds the image of this M (an
+// earlier call with the same M, P, S and img); set true once it does.
 cudaError_t launch_mode3_tc(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
                             int32_t *status, cudaStream_t st, void *img = nullptr,
-                            size_t img_bytes = 0);
+                            size_t img_bytes = 0, bool *img_ready = nullptr);
 // partial-sum slots for errp, xpart and ypart, enough for either kernel
 int64_t mode3_tc_partials(int64_t P, int64_t N);
 size_t mode3_img_bytes(int64_t P, int64_t S);
@@ -53,7 +55,7 @@ cudaError_t launch_mode3_ws(const float *Qm, int64_t sr, int64_t sc, const float
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
                             int32_t *status, void *img, size_t img_bytes, cudaStream_t st,
-                            bool *used);
+                            bool *used, bool *img_ready = nullptr);
 
 // The same tensor-core product over a batch (grid z): member z computes
 // Y[z] (P x N, row-major) = M[z] (P x S) X[z] (S x N) with M(r, c) =
@@ -105,9 +107,37 @@ cudaError_t launch_stiefel(const float *Q, const float *D, int64_t n, int64_t p,
                            float *out, cudaStream_t st, float *part = nullptr,
                            int64_t part_floats = 0);
 
+// Independent products on the warp-specialised kernel: for z < batch,
+// Y_z (P x N) = M_z (P x S) X_z (S x N) with M_z(r, c) = Mm[z sMz + r sr + c sc];
+// X_z(s, n) = X[z sXz + n ldx + s] (x_kmaj) or X[z sXz + s ldx + n];
+// Y_z(t, n) at Y[z sYz + n ldy + t] (y_trans) or Y[z sYz + t ldy + n].
+// img: at least batched_img_bytes(P, S, batch) bytes for the members' tf32
+// images.  *used = false (nothing launched) when the arguments do not suit it
+// (TMA needs 16-byte aligned bases and strides that are multiples of 4 floats).
+size_t batched_img_bytes(int64_t P, int64_t S, int64_t batch);
+cudaError_t launch_batched_ws(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                              const float *X, int64_t sXz, int64_t ldx, bool x_kmaj, float *Y,
+                              int64_t sYz, int64_t ldy, bool y_trans, int64_t P, int64_t S,
+                              int64_t N, int64_t batch, void *img, size_t img_bytes,
+                              cudaStream_t st, bool *used);
+
+// Facewise products C_t (rows x cols, row-major, faces rows*cols apart) =
+// L_t (rows x inner) R_t (inner x cols) for t < p, with L_t(i, k) =
+// L[t sLz + i sLi + k sLk] and R_t(k, j) = R[t sRz + k sRk + j sRj].  With img
+// (facewise_img_bytes of it, an image budget capped at FACEWISE_IMG_CAP or one
+// face) the faces run on the warp-specialised kernel in groups that fit it;
+// otherwise, or when the layouts do not suit it, on the one-CTA-per-tile kernel.
+constexpr size_t FACEWISE_IMG_CAP = (size_t)32 << 20;
+size_t facewise_img_bytes(int64_t rows, int64_t inner, int64_t cols, int64_t p);
+cudaError_t launch_facewise_strided(const float *L, int64_t sLi, int64_t sLk, int64_t sLz,
+                                    const float *Rm, int64_t sRk, int64_t sRj, int64_t sRz,
+                                    float *C, int64_t rows, int64_t inner, int64_t cols,
+                                    int64_t p, cudaStream_t st, void *img = nullptr,
+                                    size_t img_bytes = 0);
 // Batched facewise product C_t = A_t B_t (Def. 2.3).
 cudaError_t launch_facewise_gemm(const float *A, const float *B, float *C, int64_t n1,
-                                 int64_t m, int64_t n2, int64_t p, cudaStream_t st);
+                                 int64_t m, int64_t n2, int64_t p, cudaStream_t st,
+                                 void *img = nullptr, size_t img_bytes = 0);
 
 // ---------------------------------------------------------------- Jacobi
 struct JacobiArgs {

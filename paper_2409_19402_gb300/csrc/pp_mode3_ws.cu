@@ -180,6 +180,15 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+      : "memory");
+}
+
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
                                           uint32_t mbar) {
   asm volatile(
@@ -192,23 +201,27 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 // The image of M: for row tile ty and 32-wide chunk c (2 nst chunks per tile,
 // nst = stages), the K-major 128-byte-swizzled tf32 hi tile of
 // M(64 ty + t, 32 c + k), t < 64, k < 32, followed by its lo tile; zero outside
-// P x S.  One thread per 16-byte group of four terms.
-__global__ void prep_image_kernel(const float *__restrict__ Qm, int64_t sr, int64_t sc, int64_t P,
-                                  int64_t S, int64_t nchunk, int64_t tiles_y,
-                                  unsigned char *__restrict__ img) {
-  const int64_t total = tiles_y * nchunk * NT * 8;
+// P x S; batch members one after the other.  One thread per 16-byte group of
+// four terms.
+__global__ void prep_image_kernel(const float *__restrict__ Qm, int64_t sr, int64_t sc, int64_t sMz,
+                                  int64_t P, int64_t S, int64_t nchunk, int64_t tiles_y,
+                                  int64_t batch, unsigned char *__restrict__ img) {
+  // members z < batch, M[z](r, c) = Qm[z sMz + r sr + c sc], one after the other
+  const int64_t total = batch * tiles_y * nchunk * NT * 8;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int q = (int)(e & 7);
     const int t = (int)((e >> 3) % NT);
-    const int64_t tc = e / (8 * NT);   // tile * nchunk + chunk
+    const int64_t tc = e / (8 * NT);   // (member * tiles_y + tile) * nchunk + chunk
     const int64_t c = tc % nchunk;
-    const int64_t row = (tc / nchunk) * NT + t;
+    const int64_t zt = tc / nchunk;
+    const int64_t row = (zt % tiles_y) * NT + t;
+    const float *Mz = Qm + (zt / tiles_y) * sMz;
     float hv[4], lv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int64_t k = c * TK + 4 * q + j;
-      const float x = (row < P && k < S) ? Qm[row * sr + k * sc] : 0.f;
+      const float x = (row < P && k < S) ? Mz[row * sr + k * sc] : 0.f;
       hv[j] = tf32_rna(x);
       lv[j] = tf32_rna(x - hv[j]);
     }
@@ -220,15 +233,18 @@ __global__ void prep_image_kernel(const float *__restrict__ Qm, int64_t sr, int6
 }
 
 // KMAJ: X is contraction-contiguous (X(s, n) = X[n ldx + s]) and comes in as
-// two 128-byte-swizzled 32 x 128 boxes per stage; else X(s, n) = X[s N + n],
-// one unswizzled 128 x 64 box.  The contraction of S terms is split into nz
-// members of kchunk terms (a multiple of KC), member z writing its own
-// P x N product (the third coordinate of the Y map).
-template <bool KMAJ>
+// two 128-byte-swizzled 32 x 128 boxes per stage; else X(s, n) = X[s ldx + n],
+// one unswizzled 128 x 64 box.  There are nz members (the third coordinate of
+// the X and Y maps): with batch = 0 they split one contraction of S terms into
+// kchunk terms each (a multiple of KC; all read layer 0 of X at a term
+// offset and one image), with batch = 1 they are independent products (X
+// layer z, image z).  TRANS: Y is stored transposed, Y(t, n) at n P + t (the
+// 64 x 32 tile of a warp as two 128-byte-swizzled 32 x 32 boxes), else at t N + n.
+template <bool KMAJ, bool TRANS>
 __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap ymap,
     const __grid_constant__ CUtensorMap amap, const unsigned char *__restrict__ img, int has_y,
-    int has_ref, int P, int S, int N, int nz, int kchunk, double *__restrict__ errp,
+    int has_ref, int P, int S, int N, int nz, int kchunk, int batch, double *__restrict__ errp,
     double *__restrict__ xpart, double *__restrict__ ypart, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -253,6 +269,7 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     const int r = u - z * per;
     ty = r % tiles_y;
     tx = r / tiles_y;
+    if (batch) return nst_total;
     const int sz = S - z * kchunk;
     return ((sz < kchunk ? sz : kchunk) + KC - 1) / KC;
   };
@@ -299,13 +316,14 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
             break;
           }
           const uint32_t dst = smem_u32(xraw + xr.i * RAW), fb = smem_u32(&x_full[xr.i]);
-          const int s0 = z * kchunk + c * KC;   // first term of the stage
+          const int s0 = (batch ? 0 : z * kchunk) + c * KC;   // first term of the stage
+          const int layer = batch ? z : 0;
           mbar_expect_tx(fb, (uint32_t)RAW);
           if (KMAJ) {
-            tma_load_2d(dst, &xmap, s0, tx * TM, fb);
-            tma_load_2d(dst + RAW / 2, &xmap, s0 + TK, tx * TM, fb);
+            tma_load_3d(dst, &xmap, s0, tx * TM, layer, fb);
+            tma_load_3d(dst + RAW / 2, &xmap, s0 + TK, tx * TM, layer, fb);
           } else {
-            tma_load_2d(dst, &xmap, tx * TM, s0, fb);
+            tma_load_3d(dst, &xmap, tx * TM, s0, layer, fb);
           }
           xr.next(R);
         }
@@ -329,7 +347,8 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
             break;
           }
           mbar_expect_tx(smem_u32(&b_full[br.i]), (uint32_t)BST);
-          const int64_t stage = (int64_t)ty * nst_total + (int64_t)z * (kchunk / KC) + c;
+          const int64_t stage = batch ? ((int64_t)z * tiles_y + ty) * nst_total + c
+                                      : (int64_t)ty * nst_total + (int64_t)z * (kchunk / KC) + c;
           bulk_load(smem_u32(bimg + br.i * BST), img + stage * BST, (uint32_t)BST,
                     smem_u32(&b_full[br.i]));
           br.next(SB);
@@ -550,24 +569,47 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
           const float v = acc[q];
           if (ty * NT + q < P && pix < N) {
             y8 = fmaf(v, v, y8);
-            if (has_ref) {
+            if (!TRANS && has_ref) {
               const float d = stg[q * 32 + lane] - v;
               e8 = fmaf(d, d, e8);
             }
           }
-          stg[q * 32 + lane] = v;
+          if (!TRANS) stg[q * 32 + lane] = v;
         }
         ys += (double)y8;
         err += (double)e8;
       }
+      if (TRANS) {
+        // row `lane` (this pixel) of two 32 x 32 boxes (outputs 0-31, 32-63),
+        // 16-byte chunk j of a row at j ^ (row mod 8)
+        unsigned char *sb = reinterpret_cast<unsigned char *>(stg) + lane * 128;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<float4 *>(sb + h * 4096 + (((j ^ lane) & 7) << 4)) =
+                make_float4(acc[32 * h + 4 * j], acc[32 * h + 4 * j + 1], acc[32 * h + 4 * j + 2],
+                            acc[32 * h + 4 * j + 3]);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0 && has_y) {   // out-of-range rows and pixels are clipped by the store
-        asm volatile(
-            "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                reinterpret_cast<uint64_t>(&ymap)),
-            "r"(tx * TM + warp * 32), "r"(ty * NT), "r"(z), "r"(smem_u32(stg))
-            : "memory");
+        if (TRANS) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            asm volatile(
+                "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::
+                    "l"(reinterpret_cast<uint64_t>(&ymap)),
+                "r"(ty * NT + 32 * h), "r"(tx * TM + warp * 32), "r"(z),
+                "r"(smem_u32(stg) + (uint32_t)(h * 4096))
+                : "memory");
+        } else {
+          asm volatile(
+              "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::
+                  "l"(reinterpret_cast<uint64_t>(&ymap)),
+              "r"(tx * TM + warp * 32), "r"(ty * NT), "r"(z), "r"(smem_u32(stg))
+              : "memory");
+        }
         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
       const int64_t part = (((int64_t)z * tiles_y + ty) * tiles_x + tx) * 4 + warp;
@@ -608,35 +650,41 @@ int64_t mode3_ws_partials(int64_t P, int64_t N) {
 
 namespace {
 
-// The image of M (P x S, M(r, c) = Qm[r sr + c sc]) and one launch of the
-// kernel over nz members of kchunk terms; Y, when given, a 3-D map of nz
-// P x N products.
-template <bool KMAJ>
+// The image of M (batch members of P x S, M_z(r, c) = Qm[z sMz + r sr + c sc])
+// and one launch of the kernel over nz members (split-K members of kchunk
+// terms, or with batch the independent products); Y, when given, a 3-D map of
+// nz products.
+template <bool KMAJ, bool TRANS>
 cudaError_t run_ws(const CUtensorMap &xmap, const CUtensorMap &ymap, const CUtensorMap &amap,
-                   const float *Qm, int64_t sr, int64_t sc, bool has_y, bool has_ref, int64_t P,
-                   int64_t S, int64_t N, int64_t nz, int64_t kchunk, double *errp,
-                   double *xpart, double *ypart, int32_t *status, void *img, cudaStream_t st) {
+                   const float *Qm, int64_t sr, int64_t sc, int64_t sMz, bool has_y, bool has_ref,
+                   int64_t P, int64_t S, int64_t N, int64_t nz, int64_t kchunk, bool batch,
+                   double *errp, double *xpart, double *ypart, int32_t *status, void *img,
+                   cudaStream_t st, bool prep = true) {
   const int64_t tiles_y = (P + NT - 1) / NT, nst = (S + KC - 1) / KC, tiles_x = (N + TM - 1) / TM;
-  const int64_t total = tiles_y * 2 * nst * NT * 8;
-  int pb = (int)((total + 255) / 256);
-  if (pb > 4 * num_sms()) pb = 4 * num_sms();
-  count_launch(1);
-  prep_image_kernel<<<pb, 256, 0, st>>>(Qm, sr, sc, P, S, 2 * nst, tiles_y,
-                                        static_cast<unsigned char *>(img));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (prep) {
+    const int64_t members = batch ? nz : 1;
+    const int64_t total = members * tiles_y * 2 * nst * NT * 8;
+    int pb = (int)((total + 255) / 256);
+    if (pb > 4 * num_sms()) pb = 4 * num_sms();
+    count_launch(1);
+    prep_image_kernel<<<pb, 256, 0, st>>>(Qm, sr, sc, batch ? sMz : 0, P, S, 2 * nst, tiles_y,
+                                          members, static_cast<unsigned char *>(img));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int64_t U = nz * tiles_x * tiles_y;
   const int grid = (int)(U < num_sms() ? U : num_sms());
   count_launch(1);
-  mode3_ws_kernel<KMAJ><<<grid, THREADS, SMEM_BYTES, st>>>(
+  mode3_ws_kernel<KMAJ, TRANS><<<grid, THREADS, SMEM_BYTES, st>>>(
       xmap, ymap, amap, static_cast<const unsigned char *>(img), has_y ? 1 : 0, has_ref ? 1 : 0,
-      (int)P, (int)S, (int)N, (int)nz, (int)kchunk, errp, xpart, ypart, status);
+      (int)P, (int)S, (int)N, (int)nz, (int)kchunk, batch ? 1 : 0, errp, xpart, ypart, status);
   return cudaGetLastError();
 }
 
-template <bool KMAJ>
+template <bool KMAJ, bool TRANS>
 bool ws_attr() {
-  if (cudaFuncSetAttribute(mode3_ws_kernel<KMAJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (cudaFuncSetAttribute(mode3_ws_kernel<KMAJ, TRANS>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SMEM_BYTES) != cudaSuccess) {
     (void)cudaGetLastError();   // this device cannot host it: the caller takes the other kernel
     return false;
@@ -644,33 +692,40 @@ bool ws_attr() {
   return true;
 }
 
+constexpr int64_t DIM_MAX = (int64_t)1 << 30;
+
 }  // namespace
 
 cudaError_t launch_mode3_ws(const float *Qm, int64_t sr, int64_t sc, const float *X, float *Y,
                             int64_t P, int64_t S, int64_t N, const float *Aref, double *errp,
                             int *n_partials, double *xpart, int *n_xpart, double *ypart,
                             int32_t *status, void *img, size_t img_bytes, cudaStream_t st,
-                            bool *used) {
+                            bool *used, bool *img_ready) {
   *used = false;
-  if (!img || img_bytes < mode3_img_bytes(P, S) || P < 1 || S < 1 || N < 1 ||
-      N > ((int64_t)1 << 30) || P > ((int64_t)1 << 30) || S > ((int64_t)1 << 30) ||
-      (reinterpret_cast<uintptr_t>(img) & 15) != 0)
+  if (!img || img_bytes < mode3_img_bytes(P, S) || P < 1 || S < 1 || N < 1 || N > DIM_MAX ||
+      P > DIM_MAX || S > DIM_MAX || (reinterpret_cast<uintptr_t>(img) & 15) != 0)
     return cudaSuccess;
   CUtensorMap xmap, ymap, amap;
   std::memset(&xmap, 0, sizeof(xmap));
   std::memset(&ymap, 0, sizeof(ymap));
   std::memset(&amap, 0, sizeof(amap));
-  if (!encode_rows_2d(&xmap, X, N, S, (uint32_t)TM, (uint32_t)KC, true)) return cudaSuccess;
+  // X(s, n) = X[s N + n]: one layer of S rows, 64 x 128 boxes
+  if (!encode_3d(&xmap, X, N, S, 1, N, N * S, (uint32_t)TM, (uint32_t)KC, true, false))
+    return cudaSuccess;
   if (Y && !encode_layers_3d(&ymap, Y, N, P, 1, 32u, (uint32_t)NT)) return cudaSuccess;
   if (Aref && !encode_rows_2d(&amap, Aref, N, P, 32u, (uint32_t)NT, false)) return cudaSuccess;
-  if (!ws_attr<false>()) return cudaSuccess;
+  if (!ws_attr<false, false>()) return cudaSuccess;
   *used = true;
   const int64_t tiles_y = (P + NT - 1) / NT, tiles_x = (N + TM - 1) / TM;
   if (n_partials) *n_partials = (int)(tiles_x * tiles_y * 4);
   if (n_xpart) *n_xpart = (int)(tiles_x * NCG * 4);
   const int64_t kchunk = (S + KC - 1) / KC * KC;   // one member: the whole contraction
-  return run_ws<false>(xmap, ymap, amap, Qm, sr, sc, Y != nullptr, Aref != nullptr, P, S, N, 1,
-                       kchunk, Aref ? errp : nullptr, xpart, ypart, status, img, st);
+  const cudaError_t e =
+      run_ws<false, false>(xmap, ymap, amap, Qm, sr, sc, 0, Y != nullptr, Aref != nullptr, P, S,
+                           N, 1, kchunk, false, Aref ? errp : nullptr, xpart, ypart, status, img,
+                           st, !(img_ready && *img_ready));
+  if (img_ready && e == cudaSuccess) *img_ready = true;
+  return e;
 }
 
 size_t nt_img_bytes(int64_t R, int64_t S, int64_t K) {
@@ -687,8 +742,7 @@ cudaError_t launch_nt_ws(const float *A, const float *B, int64_t R, int64_t S, i
   const float *first = tr ? B : A, *second = tr ? A : B;
   const int64_t P = tr ? S : R, N = tr ? R : S;
   if (!img || !part || img_bytes < mode3_img_bytes(P, K) || K < 1 || P < 1 || N < 1 ||
-      K > ((int64_t)1 << 30) || N > ((int64_t)1 << 30) || K % 4 != 0 ||
-      (reinterpret_cast<uintptr_t>(img) & 15) != 0)
+      K > DIM_MAX || N > DIM_MAX || K % 4 != 0 || (reinterpret_cast<uintptr_t>(img) & 15) != 0)
     return cudaSuccess;
   // members: about one unit per SM, each at least four stages
   const int64_t per = ((N + TM - 1) / TM) * ((P + NT - 1) / NT);
@@ -704,16 +758,66 @@ cudaError_t launch_nt_ws(const float *A, const float *B, int64_t R, int64_t S, i
   std::memset(&xmap, 0, sizeof(xmap));
   std::memset(&ymap, 0, sizeof(ymap));
   std::memset(&amap, 0, sizeof(amap));
-  // X(s, n) = second[n K + s]: rows of K terms, 32 x 128 boxes with the 128-byte swizzle
-  if (!encode_rows_2d(&xmap, second, K, N, (uint32_t)TK, (uint32_t)TM, true, true))
+  // X(s, n) = second[n K + s]: one layer of N rows of K terms, 32 x 128 boxes
+  // with the 128-byte swizzle
+  if (!encode_3d(&xmap, second, K, N, 1, K, K * N, (uint32_t)TK, (uint32_t)TM, true, true))
     return cudaSuccess;
   if (!encode_layers_3d(&ymap, part, N, P, nz, 32u, (uint32_t)NT)) return cudaSuccess;
-  if (!ws_attr<true>()) return cudaSuccess;
+  if (!ws_attr<true, false>()) return cudaSuccess;
   *used = true;
   *nz_out = nz;
   *transposed = tr;
-  return run_ws<true>(xmap, ymap, amap, first, K, 1, true, false, P, K, N, nz, kchunk, nullptr,
-                      nullptr, nullptr, nullptr, img, st);
+  return run_ws<true, false>(xmap, ymap, amap, first, K, 1, 0, true, false, P, K, N, nz, kchunk,
+                             false, nullptr, nullptr, nullptr, nullptr, img, st);
+}
+
+size_t batched_img_bytes(int64_t P, int64_t S, int64_t batch) {
+  return batch < 1 ? 0 : (size_t)batch * mode3_img_bytes(P, S);
+}
+
+cudaError_t launch_batched_ws(const float *Mm, int64_t sr, int64_t sc, int64_t sMz,
+                              const float *X, int64_t sXz, int64_t ldx, bool x_kmaj, float *Y,
+                              int64_t sYz, int64_t ldy, bool y_trans, int64_t P, int64_t S,
+                              int64_t N, int64_t batch, void *img, size_t img_bytes,
+                              cudaStream_t st, bool *used) {
+  *used = false;
+  if (!img || img_bytes < batched_img_bytes(P, S, batch) || P < 1 || S < 1 || N < 1 ||
+      batch < 1 || batch > 65535 || P > DIM_MAX || S > DIM_MAX || N > DIM_MAX ||
+      (reinterpret_cast<uintptr_t>(img) & 15) != 0 || (x_kmaj ? S : N) > ldx ||
+      (y_trans ? P : N) > ldy ||
+      batch * ((N + TM - 1) / TM) * ((P + NT - 1) / NT) > (int64_t)INT32_MAX)
+    return cudaSuccess;
+  CUtensorMap xmap, ymap, amap;
+  std::memset(&xmap, 0, sizeof(xmap));
+  std::memset(&ymap, 0, sizeof(ymap));
+  std::memset(&amap, 0, sizeof(amap));
+  // X_z: rows ldx floats apart, layers sXz apart; contraction-contiguous X in
+  // swizzled 32 x 128 boxes, pixel-contiguous X in 64 x 128 boxes
+  const bool xok = x_kmaj ? encode_3d(&xmap, X, S, N, batch, ldx, sXz, (uint32_t)TK,
+                                      (uint32_t)TM, true, true)
+                          : encode_3d(&xmap, X, N, S, batch, ldx, sXz, (uint32_t)TM,
+                                      (uint32_t)KC, true, false);
+  // Y_z: a warp's tile as one 64 x 32 box, or transposed as two swizzled 32 x 32 boxes
+  const bool yok = y_trans ? encode_3d(&ymap, Y, P, N, batch, ldy, sYz, 32u, 32u, false, true)
+                           : encode_3d(&ymap, Y, N, P, batch, ldy, sYz, 32u, (uint32_t)NT, false,
+                                       false);
+  if (!xok || !yok) return cudaSuccess;
+  if (x_kmaj ? (y_trans ? !ws_attr<true, true>() : !ws_attr<true, false>())
+             : (y_trans ? !ws_attr<false, true>() : !ws_attr<false, false>()))
+    return cudaSuccess;
+  *used = true;
+  const int64_t kchunk = (S + KC - 1) / KC * KC;
+  if (x_kmaj && y_trans)
+    return run_ws<true, true>(xmap, ymap, amap, Mm, sr, sc, sMz, true, false, P, S, N, batch,
+                              kchunk, true, nullptr, nullptr, nullptr, nullptr, img, st);
+  if (x_kmaj)
+    return run_ws<true, false>(xmap, ymap, amap, Mm, sr, sc, sMz, true, false, P, S, N, batch,
+                               kchunk, true, nullptr, nullptr, nullptr, nullptr, img, st);
+  if (y_trans)
+    return run_ws<false, true>(xmap, ymap, amap, Mm, sr, sc, sMz, true, false, P, S, N, batch,
+                               kchunk, true, nullptr, nullptr, nullptr, nullptr, img, st);
+  return run_ws<false, false>(xmap, ymap, amap, Mm, sr, sc, sMz, true, false, P, S, N, batch,
+                              kchunk, true, nullptr, nullptr, nullptr, nullptr, img, st);
 }
 
 }  // namespace pp

@@ -91,3 +91,26 @@ def test_descent_step_with_retraction():
         Q1 = (Q1 * torch.sign(torch.diagonal(R))).contiguous()
         loss1 = 0.5 * ((ag.qprod(A1, B1, Q1) - Td) ** 2).sum()
     assert float(loss1) < float(loss0)
+
+
+@pytest.mark.parametrize("dims", [
+    (96, 100, 52, 36, 20),     # faces wider than tall: C_t, dA_t, dB_t stored transposed
+    (64, 36, 60, 132, 16),     # faces taller than wide: stored directly
+    (48, 8, 2048, 4, 40),      # 40 faces of 1 MB images, 32 to a launch: two launches
+])
+def test_forward_and_backward_on_the_batched_tile_layouts(dims):
+    """The facewise products of pprod and pprod_backward in each operand layout
+    of the warp-specialised kernel (contraction- or pixel-contiguous X, direct
+    or transposed store), ragged in every tile dimension, against the oracle."""
+    from paper_2409_19402_gb300 import binding
+    n, n1, m, n2, p = dims
+    A, B, Q, T = _instance(n, n1, m, n2, p, seed=11)
+    Ad, Bd, Qd, Td = (x.cuda() for x in (A, B, Q, T))
+    C = binding.pprod(Ad, Bd, Qd)
+    torch.cuda.synchronize()
+    assert _rel(C, oracle.qprod(A.numpy(), B.numpy(), Q.numpy())) <= 1e-5
+    dA, dB, dQ, dQE = binding.pprod_backward(Ad, Bd, Qd, (C - Td).contiguous(), want_euclid=True)
+    torch.cuda.synchronize()
+    _, rA, rB, rQE, rQ = oracle.qprod_grad(A.numpy(), B.numpy(), Q.numpy(), T.numpy())
+    for got, ref, name in ((dA, rA, "dA"), (dB, rB, "dB"), (dQE, rQE, "dQE"), (dQ, rQ, "dQ")):
+        assert _rel(got, ref) <= 1e-5, (name, _rel(got, ref))
