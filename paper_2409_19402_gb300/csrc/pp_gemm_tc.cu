@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(THREADS, TMA ? 1 : 2) mode3_tc_kernel(
   constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
   constexpr int TMEM_COLS = 2 * NT;   // two chunk accumulators
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // the 1024-byte aligned base, offset from smem_raw itself so that the
+  // compiler still sees shared-memory accesses (not generic ones) through it
+  unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ __align__(8) uint64_t full[TMA_STAGES];   // TMA path: raw stage filled
   __shared__ uint32_t tmem_base_sh;

@@ -247,8 +247,9 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
     int has_ref, int P, int S, int N, int nz, int kchunk, int batch, double *__restrict__ errp,
     double *__restrict__ xpart, double *__restrict__ ypart, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // the 1024-byte aligned base, offset from smem_raw itself so that the
+  // compiler still sees shared-memory accesses (not generic ones) through it
+  unsigned char *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char *bimg = smem;              // SB image stages (1024-aligned for the swizzle)
   unsigned char *xraw = smem + SB * BST;   // R raw X stages
   unsigned char *ostg = xraw + R * RAW;    // 4 warps x OB output staging tiles

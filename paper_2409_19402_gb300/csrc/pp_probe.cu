@@ -39,8 +39,9 @@ constexpr uint32_t MMA_IDESC = tc::tf32_idesc(128, MMA_N);
 
 __global__ void __launch_bounds__(128) mma_probe_kernel(int64_t reps, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char *smem = reinterpret_cast<unsigned char *>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  // the 1024-byte aligned base, offset from smem_raw itself so that the
+  // compiler still sees shared-memory accesses (not generic ones) through it
+  unsigned char *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_sh;
   const int tid = threadIdx.x;
