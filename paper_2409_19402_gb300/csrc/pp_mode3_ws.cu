@@ -171,6 +171,49 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
       "f"(v[29]), "f"(v[30]), "f"(v[31]));
 }
 
+// An FP32 pair (hi, lo) whose sum carries a running total of FP32 terms
+// without rounding loss (Knuth's branch-free two-sum: hi + e is exactly the
+// sum of hi and the term; the errors e collect in lo).  The energy partials
+// are accumulated this way, FP32 within a group of terms and exactly beyond,
+// instead of in FP64, whose pipe is narrow on this part and sat on the
+// converters' and the epilogue's critical paths.
+struct F2 {
+  float hi = 0.f, lo = 0.f;
+};
+
+__device__ __forceinline__ void f2_add(F2 &s, float b) {
+  const float t = s.hi + b;
+  const float bp = t - s.hi;
+  const float e = (s.hi - (t - bp)) + (b - bp);
+  s.hi = t;
+  s.lo += e;
+}
+
+// a + b (two-sum of the high parts, low parts added): the same result for
+// (a, b) and (b, a), so an xor-shuffle reduction leaves it in every lane
+__device__ __forceinline__ F2 f2_sum(const F2 &a, const F2 &b) {
+  F2 r;
+  const float t = a.hi + b.hi;
+  const float bp = t - a.hi;
+  const float e = (a.hi - (t - bp)) + (b.hi - bp);
+  r.hi = t;
+  r.lo = e + (a.lo + b.lo);
+  return r;
+}
+
+__device__ __forceinline__ F2 f2_warp_sum(F2 v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    F2 o;
+    o.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
+    o.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
+    v = f2_sum(v, o);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double f2_value(const F2 &v) { return (double)v.hi + (double)v.lo; }
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
                                             uint32_t mbar) {
   asm volatile(
@@ -428,7 +471,7 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       int z, ty, tx;
       const int nst = unit(u, z, ty, tx);
       const bool do_x = xpart != nullptr && ty == 0 && z == 0;
-      double xs = 0.0;
+      F2 xs;
       for (int c = 0; c < nst; ++c, ++g, xr.next(R), ar.next(SA)) {
         if (g % NCG != cg) continue;
         if (!__all_sync(0xffffffffu,
@@ -459,7 +502,7 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
         }
         __syncwarp();
         if (lane == 0) arrive(smem_u32(&x_empty[xr.i]));
-        if (do_x) {   // FP32 over 16 values, FP64 beyond
+        if (do_x) {   // FP32 over 16 values, exact beyond
           float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
@@ -468,7 +511,10 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
             q2 = fmaf(w[k], w[k], q2);
             q3 = fmaf(w[16 + k], w[16 + k], q3);
           }
-          xs += ((double)q0 + (double)q1) + ((double)q2 + (double)q3);
+          f2_add(xs, q0);
+          f2_add(xs, q1);
+          f2_add(xs, q2);
+          f2_add(xs, q3);
         }
         if (g >= SA && !__all_sync(0xffffffffu, wait_or_abort(smem_u32(&a_empty[ar.i]),
                                                                ar.ph ^ 1u, &abort_flag))) {
@@ -503,8 +549,8 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       }
       if (!ok) break;
       if (do_x) {
-        for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
-        if (lane == 0) xpart[((int64_t)tx * NCG + cg) * 4 + (warp & 3)] = xs;
+        xs = f2_warp_sum(xs);
+        if (lane == 0) xpart[((int64_t)tx * NCG + cg) * 4 + (warp & 3)] = f2_value(xs);
       }
     }
   } else {
@@ -561,9 +607,9 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
         break;
       }
       const int pix = tx * TM + warp * 32 + lane;
-      double err = 0.0, ys = 0.0;
+      F2 err, ys;
 #pragma unroll
-      for (int g8 = 0; g8 < NT; g8 += 8) {   // FP32 over 8 values, FP64 beyond
+      for (int g8 = 0; g8 < NT; g8 += 8) {   // FP32 over 8 values, exact beyond
         float e8 = 0.f, y8 = 0.f;
 #pragma unroll
         for (int q = g8; q < g8 + 8; ++q) {
@@ -577,8 +623,8 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
           }
           if (!TRANS) stg[q * 32 + lane] = v;
         }
-        ys += (double)y8;
-        err += (double)e8;
+        f2_add(ys, y8);
+        f2_add(err, e8);
       }
       if (TRANS) {
         // row `lane` (this pixel) of two 32 x 32 boxes (outputs 0-31, 32-63),
@@ -615,12 +661,12 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
       }
       const int64_t part = (((int64_t)z * tiles_y + ty) * tiles_x + tx) * 4 + warp;
       if (errp) {
-        for (int off = 16; off > 0; off >>= 1) err += __shfl_xor_sync(0xffffffffu, err, off);
-        if (lane == 0) errp[part] = err;
+        err = f2_warp_sum(err);
+        if (lane == 0) errp[part] = f2_value(err);
       }
       if (ypart) {
-        for (int off = 16; off > 0; off >>= 1) ys += __shfl_xor_sync(0xffffffffu, ys, off);
-        if (lane == 0) ypart[part] = ys;
+        ys = f2_warp_sum(ys);
+        if (lane == 0) ypart[part] = f2_value(ys);
       }
     }
     if (lane == 0) {

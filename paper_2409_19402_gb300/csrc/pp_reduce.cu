@@ -85,18 +85,31 @@ __device__ __forceinline__ double sum_partials_block(const double *partials, int
 }
 
 __global__ void __launch_bounds__(1024) report_kernel(ReportArgs a) {
+  __shared__ int32_t sw_warp[32];
   double e[3] = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (a.parts[i]) e[i] = sum_partials_block(a.parts[i], a.nparts[i]);
+  // the largest sweep count, every thread taking a share of the slices (one
+  // thread walking all of them waits for each load in turn)
+  int32_t sw = 0;
+  for (int64_t t = threadIdx.x; t < a.p; t += blockDim.x) sw = max(sw, a.sweeps[t]);
+  sw = __reduce_max_sync(0xffffffffu, sw);
+  if ((threadIdx.x & 31) == 0) sw_warp[threadIdx.x >> 5] = sw;
+  // fixed-k path: kept and discarded energies, summed like the partials
+  double kept = 0.0, disc = 0.0;
+  if (!a.sel_scal) {
+    kept = sum_partials_block(a.kept_partial, (int)a.p);
+    disc = sum_partials_block(a.disc_partial, (int)a.p);
+  }
+  __syncthreads();
   if (threadIdx.x != 0) return;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sw = max(sw, sw_warp[w]);
 #pragma unroll
   for (int i = 0; i < 3; ++i)
     if (a.parts[i]) a.sums[i] = e[i];
   pp_report r;
   r.status = *a.status;
-  int32_t sw = 0;
-  for (int64_t t = 0; t < a.p; ++t) sw = max(sw, a.sweeps[t]);
   r.sweeps = sw;
   r.normA2 = a.parts[0] ? e[0] : *a.normA2;
   r.normAh2 = a.parts[1] ? e[1] : *a.normAh2;
@@ -107,8 +120,6 @@ __global__ void __launch_bounds__(1024) report_kernel(ReportArgs a) {
     r.kept2 = a.sel_scal[0];
     r.discarded2 = a.sel_scal[1] - a.sel_scal[0];
   } else {
-    double kept = 0.0, disc = 0.0;
-    for (int64_t t = 0; t < a.p; ++t) { kept += a.kept_partial[t]; disc += a.disc_partial[t]; }
     r.K = 0;
     r.kappa = a.kappa_fixed;
     r.kept2 = kept;
@@ -118,12 +129,13 @@ __global__ void __launch_bounds__(1024) report_kernel(ReportArgs a) {
   *a.rep = r;
 }
 
-__global__ void hosvd_report_kernel(HosvdReportArgs a) {
+__global__ void hosvd_report_kernel(HosvdReportArgs a) {   // one warp
+  int32_t sw = 0;
+  for (int64_t t = threadIdx.x; t < a.p; t += 32) sw = max(sw, a.sweeps[t]);
+  sw = __reduce_max_sync(0xffffffffu, sw);
   if (threadIdx.x != 0) return;
   pp_hosvd_report r;
   r.status = *a.status;
-  int32_t sw = 0;
-  for (int64_t t = 0; t < a.p; ++t) sw = max(sw, a.sweeps[t]);
   r.sweeps = sw;
   r.k1 = a.k1;
   r.k2 = a.k2;
