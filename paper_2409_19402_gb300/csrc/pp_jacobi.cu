@@ -19,14 +19,15 @@
 // vectors into shared memory and runs one round-robin pass over their union.
 //
 // Output per slice: the converged vectors W (unnormalised: w_j = sigma_j y_j),
-// sigma descending (FP64-accumulated norms rounded to FP32), the permutation
-// sorted position -> vector index (ties: lower vector index first) and the
-// number of sweeps.  Non-convergence within max_sweeps writes PP_ENOCONV.
+// sigma descending (norms accumulated in FP32 pairs without rounding loss,
+// rounded to FP32), the permutation sorted position -> vector index (ties:
+// lower vector index first) and the number of sweeps.  Non-convergence within
+// max_sweeps writes PP_ENOCONV.
 //
-// All arithmetic is FP32 except the final norms (FP64 accumulation).  The
-// rotation angle is computed in FP32 with IEEE division and square roots;
-// FP64 is avoided in the inner loop because this part's FP64 rate is a small
-// fraction of its FP32 rate.
+// All arithmetic is FP32.  FP64 is avoided because this part's FP64 rate is a
+// small fraction of its FP32 rate: the rotation angles use FP32 (fast
+// reciprocals and square roots refined by Newton steps) and the final norms
+// exact FP32-pair sums.
 #include <cooperative_groups.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -157,21 +158,52 @@ __device__ __forceinline__ int block_or_count(int v, int *flag) {
   return s;
 }
 
+// hi + lo += b exactly up to the rounding of lo (Knuth's two-sum; the _rn
+// intrinsics keep the compiler from contracting the error-free steps)
+__device__ __forceinline__ void pair_add(float &hi, float &lo, float b) {
+  const float t = __fadd_rn(hi, b);
+  const float bp = __fsub_rn(t, hi);
+  lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(b, bp)));
+  hi = t;
+}
+
 // Singular values of one slice from its converged vectors in global memory
-// (FP64-accumulated norms rounded to FP32) and the per-slice descending sort
-// (ties: lower vector index first).  nrm is b floats of shared scratch.
+// and the per-slice descending sort (ties: lower vector index first).  nrm is
+// b floats of shared scratch.  Each squared norm is summed as an FP32 pair
+// (every square split exactly into its rounded value and rounding error,
+// two-sum accumulation and warp reduction), about as accurate as FP64
+// accumulation without the narrow FP64 pipe; its square root is sqrtf of the
+// high part corrected by one Newton step on the exact residual.
 __device__ void finish_slice(const float *Wg, int b, int a_pad, float *sig, int32_t *perm,
                              float *nrm) {
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = warp; j < b; j += nw) {
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int e = lane; e < a_pad; e += 32) {
       const float v = Wg[(int64_t)j * a_pad + e];
-      acc = fma((double)v, (double)v, acc);
+      const float sq = __fmul_rn(v, v);
+      lo = __fadd_rn(lo, fmaf(v, v, -sq));   // v*v - sq, exact
+      pair_add(hi, lo, sq);
     }
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) nrm[j] = (float)sqrt(acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ohi = __shfl_xor_sync(0xffffffffu, hi, off);
+      const float olo = __shfl_xor_sync(0xffffffffu, lo, off);
+      // the same sum in both lanes of a pair: two-sum of the high parts
+      // (exact, symmetric), low parts added
+      const float t = __fadd_rn(hi, ohi);
+      const float bp = __fsub_rn(t, hi);
+      const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(ohi, bp));
+      lo = __fadd_rn(err, __fadd_rn(lo, olo));
+      hi = t;
+    }
+    if (lane == 0) {
+      const float r = sqrtf(hi);
+      float s = r;
+      if (r > 0.f) s = fmaf(__fadd_rn(fmaf(-r, r, hi), lo), __fdiv_rn(0.5f, r), r);
+      nrm[j] = s;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < b; j += blockDim.x) {
