@@ -423,15 +423,20 @@ __global__ void __launch_bounds__(THREADS, 1) mode3_ws_kernel(
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t ta0 = tmem + ar.i * (uint32_t)ACOLS;
+          // Chunk h of the stage goes into its own accumulator, from zero, as
+          // lo.hi + hi.lo + hi.hi per 8-term K step (the small products
+          // first).  The two chunks' MMAs alternate, so consecutive MMAs never
+          // accumulate into the same TMEM columns; each accumulator takes its
+          // products in the same order as with the chunks one after the other.
 #pragma unroll
-          for (int h = 0; h < KC / TK; ++h) {
-            // chunk h of the stage: its own accumulator, from zero
-            const uint32_t td = tmem + (uint32_t)DCOL + dr.i * (uint32_t)DCOLS + (uint32_t)(h * NT);
-            const uint64_t dbh = desc0 + (uint64_t)((br.i * BST + h * BCH) >> 4);
-            const uint64_t dbl = dbh + (uint64_t)((NT * 128) >> 4);
-            const uint32_t ta = ta0 + (uint32_t)(h * 2 * TK);   // chunk h: hi, then lo
+          for (int kk = 0; kk < TK / 8; ++kk) {   // 8 tf32 of K per MMA
 #pragma unroll
-            for (int kk = 0; kk < TK / 8; ++kk) {   // 8 tf32 of K per MMA
+            for (int h = 0; h < KC / TK; ++h) {
+              const uint32_t td =
+                  tmem + (uint32_t)DCOL + dr.i * (uint32_t)DCOLS + (uint32_t)(h * NT);
+              const uint64_t dbh = desc0 + (uint64_t)((br.i * BST + h * BCH) >> 4);
+              const uint64_t dbl = dbh + (uint64_t)((NT * 128) >> 4);
+              const uint32_t ta = ta0 + (uint32_t)(h * 2 * TK);   // chunk h: hi, then lo
               mma_tf32_ta(td, ta + TK + 8 * kk, dbh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
               mma_tf32_ta(td, ta + 8 * kk, dbl + 2 * kk, IDESC, 1u);
               mma_tf32_ta(td, ta + 8 * kk, dbh + 2 * kk, IDESC, 1u);
