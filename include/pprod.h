@@ -165,7 +165,10 @@ PP_API pp_status pprod_facewise(const float *Ah, const float *Bh, int64_t n1, in
 /*
  * Projected product (Def. 3.1): C = [(A x_3 Q^T) ^ (B x_3 Q^T)] x_3 Q.
  * A is n1 x m x n, B is m x n2 x n, Q is n x p, C is n1 x n2 x n.
- * Workspace: pp_workspace_bytes(PP_OP_PPROD, {l=n1, m=m, n=n, p=p, n2=n2}).
+ * Workspace: pp_workspace_bytes(PP_OP_PPROD, {l=n1, m=m, n=n, p=p, n2=n2}):
+ * the transform-domain A-hat, B-hat, C-hat, the tf32 images of Q^T and Q
+ * (each built once per call) and a region for the facewise operands' images
+ * (at most 32 MB or one face's image; the faces then run in groups).
  */
 PP_API pp_status pprod(const float *A, const float *B, const float *Q, int64_t n1,
                 int64_t m, int64_t n2, int64_t n, int64_t p, float *C,
@@ -181,7 +184,8 @@ PP_API pp_status pprod(const float *A, const float *B, const float *Q, int64_t n
  *   dQ   = dQ_E - Q sym(Q^T dQ_E)  (projection on the tangent space of St_{n,p})
  * Sizes as in pprod; G, dA, dB have the shapes of C, A, B.  dQ_euclid and dQ
  * (n x p) may each be NULL.  Workspace: pp_workspace_bytes(PP_OP_PPROD_BWD,
- * {l = n1, m, n, p, n2}).
+ * {l = n1, m, n, p, n2}): as for pprod, plus G-hat, dA-hat, dB-hat, the
+ * split-K parts of dQ_E and the image of the smaller operand of each A B^T.
  */
 PP_API pp_status pprod_backward(const float *A, const float *B, const float *Q, const float *G,
                                 int64_t n1, int64_t m, int64_t n2, int64_t n, int64_t p,

@@ -2,9 +2,11 @@
 // warp-specialised tcgen05 kernel: Y (P x N) = M (P x S) X (S x N) over the
 // mode-3 unfolding, N = l m pixels, for the transform A x_3 Q^T of Alg. 4.1
 // step 2 and the reverse transform x_3 Q of step 4 when the caller provides a
-// small scratch buffer for M's converted image; and, with X contraction-
+// small scratch buffer for M's converted image; with X contraction-
 // contiguous and the contraction split into members, the A B^T over all
-// pixels of the Q gradient (launch_nt_ws).
+// pixels of the Q gradient (launch_nt_ws); and, with the members independent
+// products, the facewise products of Def. 2.3 in the projected product and
+// its backward, stored directly or transposed (launch_batched_ws).
 //
 // Arithmetic (the same as the one-CTA-per-tile kernel of pp_gemm_tc.cu): the
 // 3-pass split tf32 product hi.hi + hi.lo + lo.hi with hi = tf32(x) and
