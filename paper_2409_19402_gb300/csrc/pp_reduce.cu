@@ -18,6 +18,9 @@ int red_blocks() {
   return b < RED_MAX_BLOCKS ? b : RED_MAX_BLOCKS;
 }
 
+// Sum over the CTA (result in thread 0) in a fixed tree: a shuffle tree in
+// each warp, then one over the warp totals in warp 0 (FP64 adds are slow on
+// this part, so no thread walks the 32 totals one dependent add at a time).
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double red[32];
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -25,8 +28,10 @@ __device__ __forceinline__ double block_sum(double v) {
   if (lane == 0) red[warp] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  if (warp == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  }
   __syncthreads();
   return s;
 }
