@@ -136,5 +136,7 @@ def tsvdqII_c(A, Q, gamma: float):
     sk = [s[t, :rho[t]] for t in range(len(U))]
     Ahk = np.stack([(Uk[t] * sk[t]) @ Vk[t].conj().T for t in range(Ah.shape[0])])
     Ak, nA, nAh, err2, perr = _terms(A, Q, Ah, Ahk)
-    disc = float(total2 - kept2)
+    # Thm. 4.4: the discarded energy is the sum of the squared singular values
+    # every slice drops (its entries past rho[t]), summed directly
+    disc = float(sum((s[t, rho[t]:] ** 2).sum() for t in range(s.shape[0])))
     return rho, Uk, sk, Vk, Ak, s, ReportC(nA, nAh, err2, disc, perr, int(K), int(np.sum(rho)))
