@@ -59,6 +59,37 @@ def test_workspace_sizes():
     assert b.workspace_bytes(b.PP_OP_PPROD, l=4, m=5, n=6, p=2, n2=3) >= 4 * (2 * 20 + 2 * 15 + 2 * 12)
 
 
+def _img(P, S, faces=1):
+    """tf32 operand image of P x S per face: one 32 KB block (hi and lo of two
+    32-term chunks) per 64-row tile and 64-term stage."""
+    return faces * ((P + 63) // 64) * ((S + 63) // 64) * 32768
+
+
+def test_projected_product_workspace_holds_the_operand_images():
+    """pprod's workspace: the transform-domain tensors, the Q^T and Q images and
+    the facewise operands' images, the last capped at 32 MB (faces beyond run in
+    groups); host arithmetic only."""
+    b = _lib()
+    ws = lambda n1, m, n2, n, p: b.workspace_bytes(b.PP_OP_PPROD, l=n1, m=m, n=n, p=p, n2=n2)
+    # differentiation workload: 64 faces of 256 x 256 by 256 x 64 (the 64-wide
+    # side is the image's row side), 8 MB of facewise image
+    n1, m, n2, n, p = 256, 256, 64, 512, 64
+    tensors = 4 * p * (n1 * m + m * n2 + n1 * n2)
+    assert ws(n1, m, n2, n, p) >= tensors + _img(p, n) + _img(n, p) + _img(64, m, p)
+    # 1 MB images per face (8 x 2048 by 2048 x 4): 40 and 80 faces both exceed
+    # the cap, so doubling p adds only the tensors and the Q images
+    n1, m, n2, n = 8, 2048, 4, 96
+    grow = ws(n1, m, n2, n, 80) - ws(n1, m, n2, n, 40)
+    expect = (4 * 40 * (n1 * m + m * n2 + n1 * n2) + _img(80, n) - _img(40, n)
+              + _img(n, 80) - _img(n, 40))
+    assert grow == expect
+    # below the cap the region grows with the faces: 16 -> 24 faces adds 8 images
+    grow = ws(n1, m, n2, n, 24) - ws(n1, m, n2, n, 16)
+    expect = (4 * 8 * (n1 * m + m * n2 + n1 * n2) + _img(24, n) - _img(16, n)
+              + _img(n, 24) - _img(n, 16) + _img(4, m, 8))
+    assert grow == expect
+
+
 FAKE = ctypes.c_void_p(1 << 20)     # never dereferenced: the host rejects first
 
 
