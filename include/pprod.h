@@ -105,9 +105,10 @@ typedef struct pp_opts {
     int32_t reserved[3];
 } pp_opts;
 
-/* Device-written report of a decomposition call.  Energies are FP64 sums of
- * FP32 partial sums over at most 16 terms (relative error <= 16 * 2^-24); the
- * rank-deciding energies kept2 / discarded2 are FP64 sums of FP64 sigma^2. */
+/* Device-written report of a decomposition call.  Energies are sums of FP32
+ * partial sums over at most 16 terms (relative error <= 16 * 2^-24), carried
+ * beyond that without rounding loss (FP32 pairs, then FP64); the rank-deciding
+ * energies kept2 / discarded2 are FP64 sums of FP64 sigma^2. */
 typedef struct pp_report {
     int32_t status;       /* PP_OK or a device-detected pp_status                  */
     int32_t sweeps;       /* largest Jacobi sweep count over the p slices          */
